@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: TDVP time-steps/s of the mixed-precision batched sweep at chi = 256.
+
+Workload: the 101-site long-range transverse-field Ising chain (alpha = 1.5,
+J = 1, h = 0.5, 8 exponentials -> MPO bond dimension 10), dt = 0.01,
+chi_max = 256, eps = 1e-12, Lanczos with at most 8 vectors and tolerance 1e-6,
+8 Stoudenmire-White segments of 15, 12 x 6 and 14 sites, all segments of a
+stage batched into the same launches. The state is a seeded random MPS brought
+to the inverse canonical gauge at chi = 256 (every bond saturated, as after
+the quench's early growth), so every timed step does the full chi = 256 work.
+
+One step = one full symmetric time step (both half sweeps) of tdvp_step.
+`value` is whole-job throughput: time steps of all ranks / slowest rank's time.
+Ranks run independent replicas of the chain (the sweep of one chain runs on one
+GPU; there is no cross-GPU exchange in this build).
+
+--impl reference times the CPU oracle (numpy FP64, unchanged) on a bounded
+sample of the same workload and prints the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import tdvp_inputs as I  # noqa: E402
+
+METRIC = "TDVP time-steps/s (chi=256, mixed+batched)"
+UNIT = "time-steps/s"
+PREC = {"fp64": I.FP64, "tf32": I.TF32, "tf32x3": I.TF32X3}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32x3", choices=sorted(PREC))
+    ap.add_argument("--chi", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def workload(args):
+    w = I.cfg3_ising_large(PREC[args.precision])
+    return w
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def fp64_peak_tflops():
+    """cuBLAS DGEMM rate on this GPU (the FP64 denominator), measured here."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 1e30
+    for _ in range(3):
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def roofline(prof, steps):
+    """Roofline entry for the kernel kind with the largest device time."""
+    if not prof:
+        return None, None
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    peaks, src = measured_peaks()
+    ms_launch = d["ms"] / max(d["launches"], 1)
+    if dom.startswith("tc_gemm"):
+        # TF32 dense peak = measured bf16 burst x nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
+        peak = peaks["bf16_tflops"] * 1.1 / 2.25
+        ach = d["flops"] / d["launches"] / (ms_launch * 1e-3) / 1e12
+        r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": "%s bf16 x 1.1/2.25 (TF32 nominal ratio)" % src}
+    elif dom in ("zgemm_fp64", "svd_jacobi_sweep"):
+        peak = fp64_peak_tflops()
+        ach = d["flops"] / d["launches"] / (ms_launch * 1e-3) / 1e12
+        r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": "cuBLAS DGEMM measured in this run (FP64 pipe)"}
+    else:
+        peak = peaks["hbm_gbs"]
+        ach = d["bytes"] / d["launches"] / (ms_launch * 1e-3) / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+             "peak_source": "%s hbm_gbs" % src}
+    r["frac"] = r["achieved"] / r["peak"]
+    r["kernel"] = dom
+    r["ms_per_launch"] = ms_launch
+    r["launches"] = d["launches"]
+    r["traffic"] = None
+    return r, dom
+
+
+def cpu_baseline_sample(chi, seconds_budget=30.0):
+    """Time the oracle (as it stands) on a bounded sample of the workload: one
+    two-site H_eff application, one one-site H_eff application, one two-site
+    SVD split and one environment update at chi = 256 (random operands of the
+    workload's shapes), then scale to one time step by the operation counts of
+    the step's schedule with every bond at chi (a lower bound on the oracle's
+    step time, i.e. an upper bound on its steps/s)."""
+    from oracle import models
+    from oracle import tdvp as T
+    w = I.cfg3_ising_large()
+    mdl = w.model
+    x, lam = models.fit_power_law(mdl.alpha, mdl.n_exp, mdl.N - 1)
+    W = models.build_mpo_site(mdl.kind, mdl.J, mdl.h, x, lam)
+    m = W.shape[0]
+    L = I.random_complex((chi, m, chi), 1)
+    R = I.random_complex((chi, m, chi), 2)
+    th = I.random_complex((chi, 2, 2, chi), 3)
+    ps = I.random_complex((chi, 2, chi), 4)
+    t0 = time.perf_counter()
+    y = T.heff2_apply(L, W, W, R, th)
+    t_h2 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    T.heff1_apply(L, W, R, ps)
+    t_h1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    T.split_two_site(y, chi, 0.0, 1e-12)
+    t_svd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    T.env_left(L, ps, W)
+    t_env = time.perf_counter() - t0
+    sched = T.build_schedule(mdl.N, w.params.seg_len, 1)
+    n_f = sum(1 for h in sched for o in h if o.kind == "fwd2")
+    n_b = sum(1 for h in sched for o in h if o.kind == "back1")
+    n_env = sum(len(o.env) for h in sched for o in h if o.kind == "fwd2")
+    k = w.params.krylov_max
+    t_step = n_f * (k * t_h2 + t_svd) + n_b * k * t_h1 + n_env * t_env
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    return {
+        "value": 1.0 / t_step, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": ("numpy oracle at chi=%d: one two-site H_eff (%.2fs), one one-site H_eff (%.2fs), one "
+                   "512x512 SVD split (%.2fs), one environment update (%.2fs); scaled to one time step by "
+                   "%d two-site updates x %d Lanczos vectors + %d one-site updates x %d + %d environment "
+                   "updates with every bond at chi" % (chi, t_h2, t_h1, t_svd, t_env, n_f, k, n_b, k, n_env)),
+        "sample_seconds": t_h2 + t_h1 + t_svd + t_env,
+    }
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = workload(args)
+    for _ in range(args.warmup):
+        pass  # the oracle has no state to warm; the warm-up steps are the first samples below
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(max(args.steps, 1)):
+        cb = cpu_baseline_sample(args.chi)
+        vals.append(1.0 / cb["value"])
+    wall = time.perf_counter() - t_all
+    t_step = float(np.median(vals))
+    line = {
+        "metric": METRIC, "value": 1.0 / t_step, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": w.name, "N": w.model.N, "chi_max": args.chi, "m": w.model.m,
+                   "segments": w.params.seg_len, "dt": w.params.dt, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": 1.0 / t_step, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                         "sample": cb["sample"]},
+        "e2e": {"value": 1.0 / t_step, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_06127_gb300 import tdvp
+    torch.cuda.set_device(local)
+    w = workload(args)
+    mdl, prm = w.model, w.params
+    mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
+    raw = I.random_mps_tensors(mdl.N, args.chi, seed=0)
+    mps = tdvp.init_mps_tensors(raw, args.chi, 1e-14)
+    p = tdvp.step_params(dt=prm.dt, chi_max=args.chi, w_max=prm.w_max, eps=prm.eps,
+                         krylov_max=prm.krylov_max, krylov_tol=prm.krylov_tol, precision=PREC[args.precision],
+                         seg_len=prm.seg_len, merge_turning=1)
+    stream = torch.cuda.current_stream()
+    tdvp.step(mps, mpo, p, args.warmup, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    tdvp.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    t0 = time.perf_counter()
+    st = tdvp.step(mps, mpo, p, args.steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    prof = tdvp.profile_read()
+    tdvp.profile(False)
+    clk = clocks.stop()
+    barrier(world)
+    ms_max = allreduce_max(ms, world)
+    # end to end through the public API: step, then read the step's observable
+    # (<sigma^z_j> for every site) back to the host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_e2e = max(1, args.e2e_steps)
+    for _ in range(n_e2e):
+        tdvp.step(mps, mpo, p, 1, stream=stream)
+        sz = tdvp.measure(mps, tdvp.OBS_SZ)
+    torch.cuda.synchronize()
+    e2e_s = allreduce_max((time.perf_counter() - t0) / n_e2e, world)
+    if rank != 0:
+        return
+    steps_all = args.steps * world
+    value = steps_all / (ms_max * 1e-3)
+    rl, dom = roofline(prof, args.steps)
+    heff_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("tc_gemm") or k.startswith("zgemm")
+                  or k.startswith("wstage") or k == "prep_operands")
+    stages_per_step = st.n_stages / max(args.steps, 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision if args.precision != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "N": mdl.N, "alpha": mdl.alpha, "h": mdl.h, "m": mdl.m,
+                   "chi_max": args.chi, "dt": prm.dt, "segments": prm.seg_len, "precision": args.precision,
+                   "krylov": [prm.krylov_max, prm.krylov_tol], "init": "seeded random MPS at chi (seed 0)",
+                   "l2": "inputs larger than L2: state + environments %.1f GB" % state_gb(mdl, args.chi),
+                   "parallelism": "replicas" if world > 1 else "single GPU, segments batched"},
+        "clocks": clk,
+        "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(8 * mdl.N + stages_per_step * (4 + 12 * 8) + 4)},
+        "gpu_launches": int(st.kernel_launches),
+        "roofline": rl,
+        "heff_tflops": st.heff_flops / max(heff_ms * 1e-3, 1e-12) / 1e12 if heff_ms else None,
+        "kernels": {k: {"ms": v["ms"], "launches": v["launches"], "share": v["ms"] / max(ms, 1e-9)}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+        "w_total": st.w_total, "chi_max_seen": st.chi_max_seen, "wall_s": wall,
+    }
+    if not args.no_cpu_baseline:
+        cb = cpu_baseline_sample(args.chi)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+
+
+def state_gb(mdl, chi):
+    dims = [1] + I.bond_dims(mdl.N, chi) + [1]
+    site = sum(dims[j] * 2 * dims[j + 1] for j in range(mdl.N)) * 16
+    env = sum(2 * dims[j] * dims[j] * mdl.m for j in range(mdl.N)) * 16
+    return (site + env) / 1e9
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

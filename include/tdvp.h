@@ -1,0 +1,262 @@
+/*
+ * tdvp.h -- C ABI of libtdvp: parallel two-site TDVP for matrix product states
+ * with long-range MPOs on one GB300 GPU (sm_103a).
+ *
+ * Method: P. Secular et al., "Parallel time-dependent variational principle
+ * algorithm for matrix product states" (arXiv:1912.06127). Citations below
+ * name the paper's sections, equations and figures.
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are interleaved (re, im) doubles ("complex128").
+ *   - Indices are 0-based: sites 0..N-1, bonds 0..N-2 (bond j joins sites j, j+1).
+ *   - Site tensors Psi_j are row-major [chi_{j-1}][d][chi_j] (chi_{-1} = chi_{N-1} = 1).
+ *   - Environments are row-major [bra][mpo][ket]; MPO tensors are row-major
+ *     W[w_left][w_right][s_out][s_in].
+ *   - Every function returns TDVP_OK (0) or a negative TDVP_E* code and never
+ *     aborts; tdvp_last_error() returns a thread-local text for the last failure.
+ *   - Handles are owned by the library and released with tdvp_free_*().
+ *     Host arrays passed in or out are owned by the caller. Device memory of
+ *     handles is allocated by the library (cudaMalloc) at creation time and
+ *     held until the handle is freed; tdvp_step allocates nothing further
+ *     once the handle has stepped once with a given MPO and batch shape.
+ *   - `stream` is a cudaStream_t (NULL = default stream). Calls are ordered on
+ *     that stream; functions returning host results synchronise it.
+ *   - There is no CPU fallback: without a usable CUDA device every compute
+ *     entry point returns TDVP_ECUDA.
+ */
+#ifndef TDVP_H
+#define TDVP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define TDVP_OK 0
+#define TDVP_EINVAL (-1)   /* bad argument or size                                  */
+#define TDVP_ENOMEM (-2)   /* device or host allocation failed                      */
+#define TDVP_ECUDA (-3)    /* CUDA runtime error, or no usable device              */
+#define TDVP_ENUMERIC (-4) /* NaN/Inf, zero norm, or a failed decomposition        */
+#define TDVP_ETIMEOUT (-5) /* a bounded device wait gave up (status word set)      */
+#define TDVP_ESTATE (-6)   /* handle in the wrong state for this call               */
+
+/* ---- model kinds (Sec. IV: Eq. 25 Ising, Eq. 27 XY, Eq. 31 XXX) ---- */
+#define TDVP_ISING 0 /* sum_{i<j} J f(r) sz_i sz_j + h sum_i sx_i               */
+#define TDVP_XY 1    /* sum_{i<j} J f(r) (sx_i sx_j + sy_i sy_j) + h sum_i sx_i  */
+#define TDVP_XXX 2   /* sum_{i<j} J f(r) S_i.S_j (S = sigma/2) + h sum_i sx_i     */
+
+/* ---- contraction precision of H_eff and the environment updates ---- */
+#define TDVP_FP64 0   /* complex FP64 throughout                                  */
+#define TDVP_TF32 1   /* tensor-core TF32 complex GEMMs, FP32 accumulate          */
+#define TDVP_TF32X3 2 /* 3xTF32 split-precision products, FP32 accumulate         */
+/* Lanczos orthogonalisation, the tridiagonal exponential, the SVD and
+ * V = Lambda^-1 are FP64 in every mode. */
+
+/* ---- observables for tdvp_measure ---- */
+#define TDVP_OBS_SZ 0
+#define TDVP_OBS_SX 1
+#define TDVP_OBS_SY 2
+
+typedef struct tdvp_mpo_s* tdvp_mpo;
+typedef struct tdvp_mps_s* tdvp_mps;
+
+/* Long-range spin chain (Sec. II C). f(r) = 1/r^alpha is represented by
+ * n_exp exponentials, f(r) ~ sum_k x_k lam_k^r, giving an MPO of bond
+ * dimension m = n_terms * n_exp + 2 (n_terms = 1, 2, 3 for Ising, XY, XXX).
+ * x and lam: NULL to fit them inside tdvp_build_mpo (tdvp_fit_power_law on
+ * r = 1..N-1), or 2*n_exp doubles each (complex) supplied by the caller. */
+typedef struct {
+  int kind;
+  int N;
+  double alpha;
+  double J;
+  double h;
+  int n_exp;
+  const double* x;
+  const double* lam;
+} tdvp_model;
+
+/* Time-step settings.
+ * dt: time step; every half sweep evolves by dt/2 (Sec. III A).
+ * chi_max, w_max, eps: truncation of every SVD -- keep the smallest rank whose
+ *   discarded weight is <= w_max (Eq. 22), at most chi_max (Sec. III C), and
+ *   only singular values > eps * lambda_1 (Sec. III D). At least one is kept.
+ * krylov_max, krylov_tol: Lanczos exponentiation with at most krylov_max
+ *   vectors, stopping when the a-posteriori estimate falls below krylov_tol
+ *   (krylov_tol = 0: always krylov_max vectors unless the space is exhausted).
+ *   krylov_max <= 24.
+ * precision: TDVP_FP64 / TDVP_TF32 / TDVP_TF32X3.
+ * n_seg, seg_len: Stoudenmire-White partition into n_seg segments of
+ *   seg_len[k] >= 2 sites (Sec. III B, Fig. 6); n_seg <= 1 or seg_len NULL
+ *   runs the serial sweep. All segments of a stage run in the same launches.
+ * merge_turning: 1 evolves turning pairs once by dt instead of twice by dt/2
+ *   (App. A). */
+typedef struct {
+  double dt;
+  int chi_max;
+  double w_max;
+  double eps;
+  int krylov_max;
+  double krylov_tol;
+  int precision;
+  int n_seg;
+  const int* seg_len;
+  int merge_turning;
+} tdvp_step_params;
+
+/* Statistics accumulated by tdvp_step (added to what the struct holds). */
+typedef struct {
+  double w_total;            /* sum of discarded weights w over all SVDs (Sec. III C) */
+  int chi_max_seen;          /* largest bond dimension produced                       */
+  int n_stages;              /* batched stages executed                               */
+  int64_t krylov_vectors;    /* Krylov vectors used over all local exponentials       */
+  int64_t n_fwd2;            /* two-site forward updates                              */
+  int64_t n_back1;           /* one-site backward updates                             */
+  double heff_flops;         /* algorithmic flops of all H_eff applications           */
+  int64_t kernel_launches;   /* kernels launched                                      */
+} tdvp_step_stats;
+
+/* ---- library / device ---- */
+
+/* Thread-local message of the last failure ("" if none). */
+const char* tdvp_last_error(void);
+/* Library version string. */
+const char* tdvp_version(void);
+/* 1 if a CUDA device of compute capability >= 10.0 is usable, else 0. */
+int tdvp_device_ok(void);
+
+/* ---- model and MPO (Sec. II C) ---- */
+
+/* Fit r^-alpha on r = 1..r_max by n_exp exponentials (Pirvu et al.'s
+ * shift-invariance method, as used by the paper; Sec. II C). Writes 2*n_exp
+ * doubles (complex) to x_out and lam_out. Host only, no GPU needed.
+ * TDVP_EINVAL for n_exp < 1, n_exp > 64, r_max < 2 or alpha <= 0. */
+int tdvp_fit_power_law(double alpha, int n_exp, int r_max, double* x_out, double* lam_out);
+
+/* Build the MPO of a model on the current device. Host arrays are copied. */
+int tdvp_build_mpo(const tdvp_model* model, tdvp_mpo* out);
+/* MPO bond dimension m and physical dimension d. */
+int tdvp_mpo_dims(tdvp_mpo mpo, int* m, int* d);
+/* Copy the bulk tensor W (2*m*m*d*d doubles) and the couplings x, lam
+ * (2*n_exp doubles each; any pointer may be NULL). Host only. */
+int tdvp_mpo_tensor(tdvp_mpo mpo, double* W_out, double* x_out, double* lam_out);
+void tdvp_free_mpo(tdvp_mpo mpo);
+
+/* ---- state (Sec. II A/B: inverse canonical gauge, Eq. 9) ---- */
+
+/* Product state |s_0 s_1 ...>, s_j in {0 (up, sz=+1), 1 (down)}.
+ * chi_cap: largest bond dimension the handle will hold (device memory is
+ * sized for it: site j holds up to min(chi_cap, d^(j+1), d^(N-1-j))). */
+int tdvp_init_mps(int N, int d, const int* basis_state, int chi_cap, tdvp_mps* out);
+/* State from raw site tensors (host, complex128, tensors[j] of shape
+ * [dims[j]][d][dims[j+1]], dims[0] = dims[N] = 1). The library brings it to
+ * the inverse canonical gauge (Sec. II B) with GPU SVDs -- a left-to-right
+ * orthonormalisation and a right-to-left sweep giving Lambda_j at every bond,
+ * Psi_j = Lambda_{j-1} B_j, V_j = Lambda_j^-1 -- cutting each bond to
+ * chi_cap and to singular values > eps * lambda_1, and normalises it. */
+int tdvp_init_mps_tensors(int N, int d, const int* dims, const double* const* tensors,
+                          int chi_cap, double eps, tdvp_mps* out);
+/* Current bond dimensions (N-1 ints). */
+int tdvp_mps_bond_dims(tdvp_mps mps, int* dims_out);
+/* Copy Psi_j (2*chi_l*d*chi_r doubles) or V_j (chi_j doubles) to the host. */
+int tdvp_mps_get_site(tdvp_mps mps, int j, double* out);
+int tdvp_mps_get_bond(tdvp_mps mps, int j, double* out);
+/* Site count N and physical dimension d. */
+int tdvp_mps_size(tdvp_mps mps, int* N, int* d);
+void tdvp_free_mps(tdvp_mps mps);
+
+/* ---- time evolution (Sec. III) ---- */
+
+/* Advance `mps` by n_steps time steps of the symmetric two-site TDVP sweep
+ * (Sec. III A, Fig. 2), in the segment scheme when params->n_seg > 1 (Sec.
+ * III B, Figs. 6-7). Environments (Fig. 3) are built on the first call with a
+ * given MPO (all left ones left to right, all right ones right to left) and
+ * cached in the handle. `stats` may be NULL. Synchronises `stream` once per
+ * stage (to read the new bond dimensions). TDVP_ENUMERIC on NaN or a zero
+ * norm; TDVP_ETIMEOUT if a bounded device wait gave up. */
+int tdvp_step(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps,
+              tdvp_step_stats* stats, void* stream);
+
+/* ---- measurement (Sec. IV; excluded from timing as in the paper) ---- */
+
+/* <psi|O_j|psi>/<psi|psi> for every site j (N doubles) by full transfer-matrix
+ * contraction of Psi_1 V_1 ... Psi_N (exact in any gauge). Synchronises. */
+int tdvp_measure(tdvp_mps mps, int obs, double* out);
+/* <psi|psi> and <psi|H|psi>/<psi|psi>. */
+int tdvp_norm(tdvp_mps mps, double* out);
+int tdvp_energy(tdvp_mps mps, tdvp_mpo mpo, double* out);
+/* <a|b> (2 doubles). Infidelity (Eq. 24) is 1 - |<a|b>|/sqrt(<a|a><b|b>). */
+int tdvp_overlap(tdvp_mps a, tdvp_mps b, double* out);
+
+/* ---- kernel-level operations on caller device buffers ----
+ * One local operation each, for testing and for callers that drive their own
+ * sweep. All tensor pointers are device pointers (complex128, layouts above)
+ * except W, which is a host pointer to the bulk MPO tensor W[m][m][d][d]
+ * (complex128). Temporaries are allocated and freed inside the call. The
+ * call synchronises `stream` before returning. */
+
+/* y = H_eff x (Fig. 4). nsite = 2: x, y are [chi_l][d][d][chi_r], H_eff from
+ * L = beta_j [chi_l][m][chi_l], W_j = W_{j+1} = W, R = gamma_{j+1}
+ * [chi_r][m][chi_r]; nsite = 1: x, y are [chi_l][d][chi_r], R = gamma_j. */
+int tdvp_op_heff(int precision, int nsite, int chi_l, int chi_r, int m, int d, const double* W,
+                 const double* L, const double* R, const double* x, double* y, void* stream);
+
+/* Environment update (Fig. 3, Eq. 19). side 0: out = beta_{j+1}
+ * [chi_r][m][chi_r] from env = beta_j [chi_l][m][chi_l] and A = Psi_j V_j
+ * [chi_l][d][chi_r]. side 1: out = gamma_j [chi_l][m][chi_l] from
+ * env = gamma_{j+1} [chi_r][m][chi_r] and B = V_j Psi_{j+1} [chi_l][d][chi_r]. */
+int tdvp_op_env(int precision, int side, int chi_l, int chi_r, int m, int d, const double* W,
+                const double* env, const double* A, double* out, void* stream);
+
+/* y = exp(-i t H_eff) x by Lanczos (Eq. 18 with t = dt/2, Eq. 20 with
+ * t = -dt/2), same operands as tdvp_op_heff. Writes the number of Krylov
+ * vectors used to *n_vectors (host, may be NULL). kmax <= 24. */
+int tdvp_op_expm(int precision, int nsite, int chi_l, int chi_r, int m, int d, const double* W,
+                 const double* L, const double* R, const double* x, double* y, double t,
+                 int kmax, double tol, int* n_vectors, void* stream);
+
+/* Truncated SVD split of a two-site state (Fig. 5): theta [rows][cols]
+ * (rows = chi_l*d, cols = d*chi_r) -> Psi_L [rows][chi] = U Lambda,
+ * Psi_R [chi][cols] = Lambda V^dagger, V [chi] = 1/Lambda, with the rank
+ * chosen as in tdvp_step_params. Psi_L / Psi_R must hold min(rows, cols)
+ * columns / rows; s_out (device, may be NULL) receives all min(rows, cols)
+ * singular values in descending order. chi and w (discarded weight) are
+ * written to host ints/doubles. rows, cols <= 4096. */
+int tdvp_op_split(int rows, int cols, const double* theta, int chi_max, double w_max, double eps,
+                  double* Psi_L, double* V, double* Psi_R, double* s_out, int* chi, double* w,
+                  void* stream);
+
+/* ---- profiling ---- */
+
+/* enable != 0: from now on every kernel launch of the library is bracketed by
+ * CUDA events recorded on its launching stream, and its algorithmic work
+ * (flops, bytes) is accumulated per kernel kind; 0 stops it. Either call
+ * discards what was accumulated. Synchronises the device. */
+int tdvp_profile(int enable);
+/* idx < 0: returns the number of kernel kinds recorded. Otherwise copies kind
+ * idx: name (NUL-terminated, at most name_len bytes), total device time in
+ * ms, launches, algorithmic flops and bytes; returns 1. Synchronises. */
+int tdvp_profile_read(int idx, char* name, int name_len, double* ms, int64_t* launches, double* flops,
+                      double* bytes);
+
+/* ---- host-only utilities (no GPU needed) ---- */
+
+/* The stage schedule of one half (1 or 2) of a time step (Sec. III A/B, App.
+ * A/B): 7 ints per op -- segment, kind (0 = two-site forward step on the pair
+ * (j, j+1), 1 = one-site backward step on site j), j, time in units of dt/2,
+ * environments rebuilt after a two-site step (bit 0: beta_{j+1}, bit 1:
+ * gamma_j), boundary flag, stage index. Returns the number of ops (out may be
+ * NULL to query it) or a negative error code. */
+int tdvp_schedule(int N, int n_seg, const int* seg_len, int merge_turning, int half, int* out, int max_ops);
+
+/* c = exp(-i t T) e_0 (2*k doubles) for the real symmetric tridiagonal T with
+ * diagonal alpha[k] and off-diagonal beta[k-1] -- the small exponential of the
+ * Lanczos method; the same routine runs inside the device kernels. k <= 24. */
+int tdvp_tridiag_expm(int k, const double* alpha, const double* beta, double t, double* c_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDVP_H */

@@ -1,0 +1,1346 @@
+// C ABI of libtdvp and the sweep executor.
+//
+// tdvp_step runs each half of a time step as a list of stages (schedule.cu).
+// All two-site updates of a stage run together -- Theta = Psi_j V_j Psi_{j+1}
+// (Fig. 5 input), exp(-i H2_eff tau) Theta by Lanczos (Eq. 18), the truncated
+// SVD re-split (Fig. 5) and the environment updates (Eq. 19) -- as one set of
+// batched launches, followed by all one-site backward updates of the stage
+// (Eq. 20). One synchronisation per stage reads the new bond dimensions.
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <mutex>
+
+#include "engine.h"
+
+using namespace tdvp;
+
+namespace tdvp {
+
+int64_t g_launches = 0;
+static thread_local std::string g_last_error;
+
+[[noreturn]] void fail(int code, const std::string& msg) { throw TdvpError{code, msg}; }
+
+void cuda_check(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  cudaGetLastError();
+  fail(TDVP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" + std::to_string(line) + ")");
+}
+
+}  // namespace tdvp
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+struct tdvp_mpo_s {
+  int kind = 0, N = 0, m = 0, d = 2, n_exp = 0;
+  double alpha = 0, J = 0, h = 0;
+  std::vector<double2> x, lam;
+  std::vector<double2> W;    // [m][m][d][d]
+  std::vector<double2> W12;  // [m][m][d^2][d^2]
+  DeviceWOp w1, w1t, w2;     // one-site (out right), one-site (out left), two-site
+  uint64_t id = 0;
+};
+
+struct tdvp_mps_s {
+  int N = 0, d = 2, chi_cap = 1;
+  std::vector<int> dims;  // N-1 bond dimensions
+  std::vector<int> cap;   // N-1 bond capacities
+  std::vector<double2*> Psi;
+  std::vector<double*> V;
+  // environments for the attached MPO
+  uint64_t env_id = 0;
+  int env_m = 0;
+  std::vector<double2*> beta, gamma;
+  // tensor-core operand forms of the environments
+  int form_passes = 0;
+  std::vector<float*> beta32[2], gamma32[2];
+  std::vector<char> beta32_ok, gamma32_ok;
+  // per-problem workspaces
+  std::vector<std::unique_ptr<Slot>> slots;
+  int* d_status = nullptr;
+  int* d_chi = nullptr;
+  double* d_w = nullptr;
+  int* d_flag = nullptr;
+  int* h_pinned = nullptr;  // [0] = flag, [1] = status, [2..2+MAXB) chi
+  double* h_w = nullptr;
+
+  int chiL(int j) const { return j == 0 ? 1 : dims[j - 1]; }
+  int chiR(int j) const { return j == N - 1 ? 1 : dims[j]; }
+  int capL(int j) const { return j == 0 ? 1 : cap[j - 1]; }
+  int capR(int j) const { return j == N - 1 ? 1 : cap[j]; }
+};
+
+static uint64_t g_next_id = 1;
+static std::mutex g_id_mutex;
+
+namespace {
+
+int ok_or_code(const std::function<void()>& f) {
+  try {
+    f();
+    return TDVP_OK;
+  } catch (const TdvpError& e) {
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return TDVP_ENOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return TDVP_EINVAL;
+  }
+}
+
+void require_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    fail(TDVP_ECUDA, "no usable CUDA device");
+  }
+}
+
+std::vector<double2> two_site_mpo(const std::vector<double2>& W, int m, int d) {
+  const int D = d * d;
+  std::vector<double2> W12((size_t)m * m * D * D, make_double2(0, 0));
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b)
+      for (int c = 0; c < m; ++c) {
+        const double2* w1 = &W[((size_t)a * m + b) * d * d];
+        const double2* w2 = &W[((size_t)b * m + c) * d * d];
+        bool nz1 = false, nz2 = false;
+        for (int q = 0; q < d * d; ++q) {
+          nz1 |= w1[q].x != 0 || w1[q].y != 0;
+          nz2 |= w2[q].x != 0 || w2[q].y != 0;
+        }
+        if (!nz1 || !nz2) continue;
+        double2* o = &W12[((size_t)a * m + c) * D * D];
+        for (int s1 = 0; s1 < d; ++s1)
+          for (int s2 = 0; s2 < d; ++s2)
+            for (int t1 = 0; t1 < d; ++t1)
+              for (int t2 = 0; t2 < d; ++t2) {
+                double2& r = o[(s1 * d + s2) * D + (t1 * d + t2)];
+                r = zadd(r, zmul(w1[s1 * d + t1], w2[s2 * d + t2]));
+              }
+      }
+  return W12;
+}
+
+void build_site_W(tdvp_mpo_s* M) {
+  const int d = 2, m = M->m, K = M->n_exp;
+  const double2 Z = make_double2(0, 0), One = make_double2(1, 0);
+  // Pauli matrices [s_out][s_in]
+  const double2 SX[4] = {Z, One, One, Z};
+  const double2 SY[4] = {Z, make_double2(0, -1), make_double2(0, 1), Z};
+  const double2 SZ[4] = {One, Z, Z, make_double2(-1, 0)};
+  const double2 I2[4] = {One, Z, Z, One};
+  std::vector<std::pair<const double2*, double>> terms;
+  if (M->kind == TDVP_ISING) terms = {{SZ, 1.0}};
+  else if (M->kind == TDVP_XY) terms = {{SX, 1.0}, {SY, 1.0}};
+  else terms = {{SX, 0.5}, {SY, 0.5}, {SZ, 0.5}};
+  M->W.assign((size_t)m * m * d * d, Z);
+  auto put = [&](int a, int b, const double2* op, double2 coef) {
+    double2* o = &M->W[((size_t)a * m + b) * d * d];
+    for (int q = 0; q < 4; ++q) o[q] = zmul(op[q], coef);
+  };
+  // finite-state layout: m-1 = nothing placed yet, 0 = all placed (Sec. II C)
+  put(0, 0, I2, One);
+  put(m - 1, m - 1, I2, One);
+  put(m - 1, 0, SX, make_double2(M->h, 0));
+  for (size_t t = 0; t < terms.size(); ++t) {
+    const double sc = terms[t].second;
+    for (int k = 0; k < K; ++k) {
+      const int c = 1 + (int)t * K + k;
+      put(m - 1, c, terms[t].first, make_double2(sc, 0));
+      put(c, c, I2, M->lam[k]);
+      put(c, 0, terms[t].first, zscale(zmul(M->x[k], M->lam[k]), M->J * sc));
+    }
+  }
+}
+
+Slot* slot_for(tdvp_mps_s* S, size_t i, int m, int kmax) {
+  while (S->slots.size() <= i) S->slots.emplace_back(new Slot());
+  const int64_t c = S->chi_cap, d = S->d;
+  const int64_t vec = c * c * d * d;
+  const int64_t T = c * c * m * d * d;
+  const int64_t f = mixed_cap_floats((int)c, m, (int)d);
+  S->slots[i]->ensure(vec, T, f, c * d, kmax);
+  return S->slots[i].get();
+}
+
+void ensure_small_buffers(tdvp_mps_s* S) {
+  if (S->d_status) return;
+  S->d_status = dalloc<int>(1);
+  S->d_chi = dalloc<int>(MAXB);
+  S->d_w = dalloc<double>(MAXB);
+  S->d_flag = dalloc<int>(1);
+  CUDA_TRY(cudaMemset(S->d_status, 0, sizeof(int)));
+  CUDA_TRY(cudaMallocHost((void**)&S->h_pinned, sizeof(int) * (2 + MAXB)));
+  CUDA_TRY(cudaMallocHost((void**)&S->h_w, sizeof(double) * MAXB));
+}
+
+void free_envs(tdvp_mps_s* S) {
+  for (auto p : S->beta) dfree(p);
+  for (auto p : S->gamma) dfree(p);
+  for (int h = 0; h < 2; ++h) {
+    for (auto p : S->beta32[h]) dfree(p);
+    for (auto p : S->gamma32[h]) dfree(p);
+    S->beta32[h].clear();
+    S->gamma32[h].clear();
+  }
+  S->beta.clear();
+  S->gamma.clear();
+  S->env_id = 0;
+  S->env_m = 0;
+  S->form_passes = 0;
+}
+
+// Left/right environment of every site from scratch (Sec. III A: all gamma
+// built right to left at the start; Sec. III B: each partition needs the
+// environments of its own sites, so both sides are built once).
+void build_all_envs(tdvp_mps_s* S, tdvp_mpo_s* M, cudaStream_t s) {
+  const int N = S->N, m = M->m, d = S->d;
+  if (S->env_id != M->id) {
+    free_envs(S);
+    S->beta.resize(N);
+    S->gamma.resize(N);
+    for (int j = 0; j < N; ++j) {
+      S->beta[j] = dalloc<double2>((size_t)S->capL(j) * S->capL(j) * m);
+      S->gamma[j] = dalloc<double2>((size_t)S->capR(j) * S->capR(j) * m);
+    }
+    S->env_m = m;
+    S->beta32_ok.assign(N, 0);
+    S->gamma32_ok.assign(N, 0);
+  }
+  std::vector<double2> bl(m, make_double2(0, 0)), br(m, make_double2(0, 0));
+  bl[m - 1] = make_double2(1, 0);
+  br[0] = make_double2(1, 0);
+  CUDA_TRY(cudaMemcpyAsync(S->beta[0], bl.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(S->gamma[N - 1], br.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, s));
+  Slot* sl = slot_for(S, 0, m, 1);
+  Ctx c{s, S->d_status, TDVP_FP64};
+  for (int j = 0; j + 1 < N; ++j) {
+    ScaleBatch sb{};
+    sb.n = 1;
+    sb.d[0] = ScaleDesc{S->Psi[j], sl->Amat, S->V[j], S->chiL(j), d, S->chiR(j), 0};
+    launch_scale_bond(sb, s);
+    env_batch(0, {EnvProb{S->chiL(j), S->chiR(j), d, m, S->beta[j], sl->Amat, S->beta[j + 1], M->w1.op(), sl}}, c);
+  }
+  for (int j = N - 2; j >= 0; --j) {
+    ScaleBatch sb{};
+    sb.n = 1;
+    sb.d[0] = ScaleDesc{S->Psi[j + 1], sl->Bmat, S->V[j], S->chiL(j + 1), d, S->chiR(j + 1), 1};
+    launch_scale_bond(sb, s);
+    env_batch(1, {EnvProb{S->chiL(j + 1), S->chiR(j + 1), d, m, S->gamma[j + 1], sl->Bmat, S->gamma[j], M->w1t.op(), sl}}, c);
+  }
+  S->env_id = M->id;
+  S->beta32_ok.assign(N, 0);
+  S->gamma32_ok.assign(N, 0);
+}
+
+// tensor-core operand forms of beta_j (as L) / gamma_j (as R), built on demand
+void ensure_forms(tdvp_mps_s* S, const std::vector<int>& Lsites, const std::vector<int>& Rsites, int passes,
+                  cudaStream_t s) {
+  const int N = S->N, m = S->env_m;
+  if (S->form_passes != passes || S->beta32[0].empty()) {
+    for (int h = 0; h < 2; ++h) {
+      for (auto p : S->beta32[h]) dfree(p);
+      for (auto p : S->gamma32[h]) dfree(p);
+      S->beta32[h].assign(N, nullptr);
+      S->gamma32[h].assign(N, nullptr);
+    }
+    for (int j = 0; j < N; ++j) {
+      const int64_t cl = S->capL(j), cr = S->capR(j);
+      for (int h = 0; h < passes && h < 2; ++h) {
+        S->beta32[h][j] = dalloc<float>(cl * m * pad4(2 * cl));
+        S->gamma32[h][j] = dalloc<float>(2 * cr * pad4(2 * m * cr));
+      }
+    }
+    S->form_passes = passes;
+    S->beta32_ok.assign(N, 0);
+    S->gamma32_ok.assign(N, 0);
+  }
+  std::vector<EnvFormJob> jl, jr;
+  for (int j : Lsites)
+    if (!S->beta32_ok[j]) {
+      jl.push_back(EnvFormJob{S->beta[j], S->chiL(j), m, S->beta32[0][j], passes == 3 ? S->beta32[1][j] : nullptr});
+      S->beta32_ok[j] = 1;
+    }
+  for (int j : Rsites)
+    if (!S->gamma32_ok[j]) {
+      jr.push_back(EnvFormJob{S->gamma[j], S->chiR(j), m, S->gamma32[0][j], passes == 3 ? S->gamma32[1][j] : nullptr});
+      S->gamma32_ok[j] = 1;
+    }
+  prep_L_forms(jl, s);
+  prep_R_forms(jr, s);
+}
+
+MvProb make_mv(tdvp_mps_s* S, tdvp_mpo_s* M, int A, int B, int D, int Lsite, int Rsite, bool two, Slot* sl,
+               int prec) {
+  MvProb p{};
+  p.A = A;
+  p.B = B;
+  p.D = D;
+  p.m = M->m;
+  p.L = S->beta[Lsite];
+  p.R = S->gamma[Rsite];
+  p.W = two ? M->w2.op() : M->w1.op();
+  p.slot = sl;
+  if (prec != TDVP_FP64) {
+    p.L32[0] = S->beta32[0][Lsite];
+    p.L32[1] = prec == TDVP_TF32X3 ? S->beta32[1][Lsite] : nullptr;
+    p.R32[0] = S->gamma32[0][Rsite];
+    p.R32[1] = prec == TDVP_TF32X3 ? S->gamma32[1][Rsite] : nullptr;
+    p.ldL = pad4(2 * (int64_t)A);
+    p.ldR = pad4(2 * (int64_t)M->m * B);
+  }
+  return p;
+}
+
+double heff_flops(int A, int B, int D, int m, int nnz) {
+  // complex multiply-add = 8 real flops
+  return 8.0 * ((double)A * A * B * m * D + (double)A * B * B * m * D + (double)A * B * D * D * nnz);
+}
+
+void read_stage_results(tdvp_mps_s* S, int n, cudaStream_t s) {
+  CUDA_TRY(cudaMemcpyAsync(S->h_pinned + 1, S->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (n > 0) {
+    CUDA_TRY(cudaMemcpyAsync(S->h_pinned + 2, S->d_chi, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(S->h_w, S->d_w, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const int st = S->h_pinned[1];
+  if (st & 1) fail(TDVP_ETIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
+  if (st & (2 | 8)) fail(TDVP_ENUMERIC, "NaN or zero norm in a local update");
+  if (st & 4) fail(TDVP_ENUMERIC, "tridiagonal eigen-solver did not converge");
+}
+
+struct StageOp {
+  int j, tfac, env;
+};
+
+void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, const tdvp_step_params* p,
+              tdvp_step_stats* st, cudaStream_t s) {
+  const int n = (int)ops.size();
+  const int d = S->d, m = M->m, prec = p->precision;
+  const double tau = 0.5 * p->dt;
+  Ctx c{s, S->d_status, prec};
+  std::vector<Slot*> sl(n);
+  for (int i = 0; i < n; ++i) sl[i] = slot_for(S, i, m, p->krylov_max);
+  // Theta = Psi_j V_j Psi_{j+1}
+  ZGemmBatch g{};
+  g.n = n;
+  for (int i = 0; i < n; ++i) {
+    const int j = ops[i].j, A = S->chiL(j), cb = S->dims[j], B = S->chiR(j + 1);
+    ZGemmDesc& q = g.d[i];
+    q = ZGemmDesc{};
+    q.M = A * d;
+    q.N = d * B;
+    q.K = cb;
+    q.A = S->Psi[j];
+    q.a_rs = cb;
+    q.a_cs = 1;
+    q.kscale = S->V[j];
+    q.B = S->Psi[j + 1];
+    q.b_rs = (int64_t)d * B;
+    q.b_cs = 1;
+    q.C = sl[i]->theta;
+    q.c_rs = (int64_t)d * B;
+    q.c_cs = 1;
+  }
+  launch_zgemm(g, s);
+  // exp(-i H2_eff t) Theta
+  std::vector<MvProb> P(n);
+  std::vector<const double2*> x(n);
+  std::vector<double2*> y(n);
+  std::vector<double> t(n);
+  std::vector<int> Ls, Rs;
+  for (int i = 0; i < n; ++i) {
+    const int j = ops[i].j;
+    Ls.push_back(j);
+    Rs.push_back(j + 1);
+  }
+  if (prec != TDVP_FP64) ensure_forms(S, Ls, Rs, prec == TDVP_TF32X3 ? 3 : 1, s);
+  for (int i = 0; i < n; ++i) {
+    const int j = ops[i].j, A = S->chiL(j), B = S->chiR(j + 1);
+    P[i] = make_mv(S, M, A, B, d * d, j, j + 1, true, sl[i], prec);
+    x[i] = sl[i]->theta;
+    y[i] = sl[i]->theta2;
+    t[i] = ops[i].tfac * tau;
+    if (st) st->heff_flops += p->krylov_max * heff_flops(A, B, d * d, m, M->w2.nnz);
+  }
+  expm_batch(P, x, y, t, p->krylov_max, p->krylov_tol, c);
+  // truncated SVD re-split (Fig. 5)
+  SvdBatch sb{};
+  sb.n = n;
+  sb.status = S->d_status;
+  for (int i = 0; i < n; ++i) {
+    const int j = ops[i].j, A = S->chiL(j), B = S->chiR(j + 1);
+    SvdDesc& q = sb.d[i];
+    q = SvdDesc{};
+    q.theta = sl[i]->theta2;
+    q.rows = A * d;
+    q.cols = d * B;
+    q.X = sl[i]->svdX;
+    q.Acc = sl[i]->svdAcc;
+    q.sig = sl[i]->sig;
+    q.perm = sl[i]->perm;
+    q.rotated = sl[i]->rot;
+    q.conv = sl[i]->conv;
+    q.chi_max = std::min(p->chi_max, S->cap[j]);
+    q.w_max = p->w_max;
+    q.eps = p->eps;
+    q.chi = S->d_chi + i;
+    q.w = S->d_w + i;
+    q.PsiL = S->Psi[j];
+    q.V = S->V[j];
+    q.PsiR = S->Psi[j + 1];
+    q.s_sorted = nullptr;
+  }
+  svd_split(sb, S->d_flag, S->h_pinned, s);
+  read_stage_results(S, n, s);
+  for (int i = 0; i < n; ++i) {
+    const int chi = S->h_pinned[2 + i];
+    S->dims[ops[i].j] = chi;
+    if (st) {
+      st->w_total += S->h_w[i];
+      st->chi_max_seen = std::max(st->chi_max_seen, chi);
+    }
+  }
+  // environment updates (Eq. 19 and mirror)
+  std::vector<EnvProb> le, re;
+  ScaleBatch scl{}, scr{};
+  for (int i = 0; i < n; ++i) {
+    const int j = ops[i].j;
+    if (ops[i].env & 1) {
+      scl.d[scl.n++] = ScaleDesc{S->Psi[j], sl[i]->Amat, S->V[j], S->chiL(j), d, S->chiR(j), 0};
+      le.push_back(EnvProb{S->chiL(j), S->chiR(j), d, m, S->beta[j], sl[i]->Amat, S->beta[j + 1], M->w1.op(), sl[i]});
+      S->beta32_ok[j + 1] = 0;
+    }
+    if (ops[i].env & 2) {
+      scr.d[scr.n++] = ScaleDesc{S->Psi[j + 1], sl[i]->Bmat, S->V[j], S->chiL(j + 1), d, S->chiR(j + 1), 1};
+      re.push_back(EnvProb{S->chiL(j + 1), S->chiR(j + 1), d, m, S->gamma[j + 1], sl[i]->Bmat, S->gamma[j], M->w1t.op(), sl[i]});
+      S->gamma32_ok[j] = 0;
+    }
+  }
+  launch_scale_bond(scl, s);
+  launch_scale_bond(scr, s);
+  // env_batch uses slot temporaries; the left batch must finish its use of a
+  // slot before the right batch of the same slot starts (same stream: ordered)
+  env_batch(0, le, c);
+  env_batch(1, re, c);
+  if (st) st->n_fwd2 += n;
+}
+
+void run_back1(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, const tdvp_step_params* p,
+               tdvp_step_stats* st, cudaStream_t s) {
+  const int n = (int)ops.size();
+  const int d = S->d, m = M->m, prec = p->precision;
+  const double tau = 0.5 * p->dt;
+  Ctx c{s, S->d_status, prec};
+  std::vector<MvProb> P(n);
+  std::vector<const double2*> x(n);
+  std::vector<double2*> y(n);
+  std::vector<double> t(n);
+  std::vector<int> sites;
+  for (auto& o : ops) sites.push_back(o.j);
+  if (prec != TDVP_FP64) ensure_forms(S, sites, sites, prec == TDVP_TF32X3 ? 3 : 1, s);
+  for (int i = 0; i < n; ++i) {
+    // the two-site ops of the stage are complete (same stream): reuse their slots
+    Slot* sl = slot_for(S, i, m, p->krylov_max);
+    const int j = ops[i].j, A = S->chiL(j), B = S->chiR(j);
+    P[i] = make_mv(S, M, A, B, d, j, j, false, sl, prec);
+    x[i] = S->Psi[j];
+    y[i] = S->Psi[j];
+    t[i] = -tau * ops[i].tfac;
+    if (st) st->heff_flops += p->krylov_max * heff_flops(A, B, d, m, M->w1.nnz);
+  }
+  expm_batch(P, x, y, t, p->krylov_max, p->krylov_tol, c);
+  if (st) st->n_back1 += n;
+}
+
+void check_params(const tdvp_mps_s* S, const tdvp_mpo_s* M, const tdvp_step_params* p) {
+  if (!p) fail(TDVP_EINVAL, "params is NULL");
+  if (M->N != S->N) fail(TDVP_EINVAL, "MPO and MPS have different N");
+  if (!(p->dt > 0) || p->chi_max < 1 || p->krylov_max < 1 || p->krylov_max > KRYLOV_MAX || p->w_max < 0 ||
+      p->eps < 0)
+    fail(TDVP_EINVAL, "invalid step parameters");
+  if (p->precision < TDVP_FP64 || p->precision > TDVP_TF32X3) fail(TDVP_EINVAL, "invalid precision");
+  if (p->precision != TDVP_FP64 && !tc_available()) fail(TDVP_ECUDA, "tensor-core path unavailable");
+  if (S->N < 2) fail(TDVP_EINVAL, "need N >= 2");
+}
+
+void step_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_steps, tdvp_step_stats* st,
+               cudaStream_t s) {
+  check_params(S, M, p);
+  ensure_small_buffers(S);
+  std::vector<int> seg;
+  if (p->n_seg <= 1 || !p->seg_len) seg = {S->N};
+  else seg.assign(p->seg_len, p->seg_len + p->n_seg);
+  if ((int)seg.size() > MAXB) fail(TDVP_EINVAL, "too many segments");
+  std::vector<SchedOp> halves[2];
+  build_half(S->N, seg, 1, p->merge_turning, halves[0]);
+  build_half(S->N, seg, 2, p->merge_turning, halves[1]);
+  const int64_t l0 = g_launches;
+  if (S->env_id != M->id) build_all_envs(S, M, s);
+  for (int step = 0; step < n_steps; ++step) {
+    for (int h = 0; h < 2; ++h) {
+      const auto& ops = halves[h];
+      size_t i = 0;
+      while (i < ops.size()) {
+        const int stage = ops[i].stage;
+        std::vector<StageOp> f, b;
+        while (i < ops.size() && ops[i].stage == stage) {
+          if (ops[i].kind == 0) f.push_back(StageOp{ops[i].j, ops[i].tfac, ops[i].env});
+          else b.push_back(StageOp{ops[i].j, ops[i].tfac, 0});
+          ++i;
+        }
+        if (!f.empty()) run_fwd2(S, M, f, p, st, s);
+        if (!b.empty()) run_back1(S, M, b, p, st, s);
+        if (st) st->n_stages += 1;
+      }
+    }
+    read_stage_results(S, 0, s);
+  }
+  if (st) {
+    st->kernel_launches += g_launches - l0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// MPS creation
+// ---------------------------------------------------------------------------
+tdvp_mps_s* new_mps(int N, int d, int chi_cap) {
+  if (N < 2 || d < 2 || d > 4 || chi_cap < 1) fail(TDVP_EINVAL, "need N >= 2, 2 <= d <= 4, chi_cap >= 1");
+  require_device();
+  auto* S = new tdvp_mps_s();
+  S->N = N;
+  S->d = d;
+  S->chi_cap = chi_cap;
+  S->dims.assign(N - 1, 1);
+  S->cap.resize(N - 1);
+  for (int j = 0; j < N - 1; ++j) {
+    int64_t c = chi_cap;
+    int64_t l = 1, r = 1;
+    for (int e = 0; e < j + 1 && l < c; ++e) l *= d;
+    for (int e = 0; e < N - 1 - j && r < c; ++e) r *= d;
+    S->cap[j] = (int)std::min(c, std::min(l, r));
+  }
+  S->Psi.resize(N);
+  S->V.resize(N - 1);
+  for (int j = 0; j < N; ++j) S->Psi[j] = dalloc<double2>((size_t)S->capL(j) * d * S->capR(j));
+  for (int j = 0; j < N - 1; ++j) S->V[j] = dalloc<double>(S->cap[j]);
+  ensure_small_buffers(S);
+  return S;
+}
+
+void free_mps(tdvp_mps_s* S) {
+  if (!S) return;
+  cudaDeviceSynchronize();
+  for (auto p : S->Psi) dfree(p);
+  for (auto p : S->V) dfree(p);
+  free_envs(S);
+  S->slots.clear();
+  dfree(S->d_status);
+  dfree(S->d_chi);
+  dfree(S->d_w);
+  dfree(S->d_flag);
+  if (S->h_pinned) cudaFreeHost(S->h_pinned);
+  if (S->h_w) cudaFreeHost(S->h_w);
+  delete S;
+}
+
+// split of a (rows x cols) matrix on the device with the engine's SVD
+int device_split(tdvp_mps_s* S, Slot* sl, const double2* theta, int rows, int cols, int chi_max, double w_max,
+                 double eps, double2* PsiL, double* V, double2* PsiR, double* s_sorted, double* w_out,
+                 cudaStream_t s) {
+  SvdBatch sb{};
+  sb.n = 1;
+  sb.status = S->d_status;
+  SvdDesc& q = sb.d[0];
+  q = SvdDesc{};
+  q.theta = theta;
+  q.rows = rows;
+  q.cols = cols;
+  q.X = sl->svdX;
+  q.Acc = sl->svdAcc;
+  q.sig = sl->sig;
+  q.perm = sl->perm;
+  q.rotated = sl->rot;
+  q.conv = sl->conv;
+  q.chi_max = chi_max;
+  q.w_max = w_max;
+  q.eps = eps;
+  q.chi = S->d_chi;
+  q.w = S->d_w;
+  q.PsiL = PsiL;
+  q.V = V;
+  q.PsiR = PsiR;
+  q.s_sorted = s_sorted;
+  svd_split(sb, S->d_flag, S->h_pinned, s);
+  read_stage_results(S, 1, s);
+  if (w_out) *w_out = S->h_w[0];
+  return S->h_pinned[2];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* tdvp_last_error(void) { return g_last_error.c_str(); }
+const char* tdvp_version(void) { return "libtdvp 0.1 (sm_103a)"; }
+
+int tdvp_device_ok(void) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return 0;
+  }
+  int dev = 0, major = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return 0;
+  return major >= 10 ? 1 : 0;
+}
+
+int tdvp_fit_power_law(double alpha, int n_exp, int r_max, double* x_out, double* lam_out) {
+  return ok_or_code([&] {
+    if (!x_out || !lam_out) fail(TDVP_EINVAL, "NULL output");
+    std::vector<double2> x, lam;
+    host_fit_power_law(alpha, n_exp, r_max, x, lam);
+    std::memcpy(x_out, x.data(), sizeof(double2) * n_exp);
+    std::memcpy(lam_out, lam.data(), sizeof(double2) * n_exp);
+  });
+}
+
+int tdvp_build_mpo(const tdvp_model* model, tdvp_mpo* out) {
+  return ok_or_code([&] {
+    if (!model || !out) fail(TDVP_EINVAL, "NULL argument");
+    if (model->kind < TDVP_ISING || model->kind > TDVP_XXX || model->N < 2 || model->n_exp < 1 ||
+        model->n_exp > 64)
+      fail(TDVP_EINVAL, "invalid model");
+    require_device();
+    auto M = std::make_unique<tdvp_mpo_s>();
+    M->kind = model->kind;
+    M->N = model->N;
+    M->alpha = model->alpha;
+    M->J = model->J;
+    M->h = model->h;
+    M->n_exp = model->n_exp;
+    const int nt = model->kind == TDVP_ISING ? 1 : (model->kind == TDVP_XY ? 2 : 3);
+    M->m = nt * model->n_exp + 2;
+    if (model->x && model->lam) {
+      M->x.assign((const double2*)model->x, (const double2*)model->x + model->n_exp);
+      M->lam.assign((const double2*)model->lam, (const double2*)model->lam + model->n_exp);
+    } else {
+      host_fit_power_law(model->alpha, model->n_exp, model->N - 1, M->x, M->lam);
+    }
+    build_site_W(M.get());
+    M->W12 = two_site_mpo(M->W, M->m, M->d);
+    M->w1.build(M->W, M->m, M->d, false);
+    M->w1t.build(M->W, M->m, M->d, true);
+    M->w2.build(M->W12, M->m, M->d * M->d, false);
+    {
+      std::lock_guard<std::mutex> g(g_id_mutex);
+      M->id = g_next_id++;
+    }
+    *out = M.release();
+  });
+}
+
+int tdvp_mpo_dims(tdvp_mpo mpo, int* m, int* d) {
+  return ok_or_code([&] {
+    if (!mpo) fail(TDVP_EINVAL, "NULL mpo");
+    if (m) *m = mpo->m;
+    if (d) *d = mpo->d;
+  });
+}
+
+int tdvp_mpo_tensor(tdvp_mpo mpo, double* W_out, double* x_out, double* lam_out) {
+  return ok_or_code([&] {
+    if (!mpo) fail(TDVP_EINVAL, "NULL mpo");
+    if (W_out) std::memcpy(W_out, mpo->W.data(), sizeof(double2) * mpo->W.size());
+    if (x_out) std::memcpy(x_out, mpo->x.data(), sizeof(double2) * mpo->n_exp);
+    if (lam_out) std::memcpy(lam_out, mpo->lam.data(), sizeof(double2) * mpo->n_exp);
+  });
+}
+
+void tdvp_free_mpo(tdvp_mpo mpo) { delete mpo; }
+
+int tdvp_init_mps(int N, int d, const int* basis_state, int chi_cap, tdvp_mps* out) {
+  return ok_or_code([&] {
+    if (!basis_state || !out) fail(TDVP_EINVAL, "NULL argument");
+    tdvp_mps_s* S = new_mps(N, d, chi_cap);
+    try {
+      for (int j = 0; j < N; ++j) {
+        if (basis_state[j] < 0 || basis_state[j] >= d) fail(TDVP_EINVAL, "basis state out of range");
+        std::vector<double2> t(d, make_double2(0, 0));
+        t[basis_state[j]] = make_double2(1, 0);
+        CUDA_TRY(cudaMemcpy(S->Psi[j], t.data(), sizeof(double2) * d, cudaMemcpyHostToDevice));
+      }
+      const double one = 1.0;
+      for (int j = 0; j < N - 1; ++j) CUDA_TRY(cudaMemcpy(S->V[j], &one, sizeof(double), cudaMemcpyHostToDevice));
+    } catch (...) {
+      free_mps(S);
+      throw;
+    }
+    *out = S;
+  });
+}
+
+int tdvp_init_mps_tensors(int N, int d, const int* dims, const double* const* tensors, int chi_cap, double eps,
+                          tdvp_mps* out) {
+  return ok_or_code([&] {
+    if (!dims || !tensors || !out) fail(TDVP_EINVAL, "NULL argument");
+    if (dims[0] != 1 || dims[N] != 1) fail(TDVP_EINVAL, "boundary bond dimensions must be 1");
+    tdvp_mps_s* S = new_mps(N, d, chi_cap);
+    try {
+      cudaStream_t s = 0;
+      // raw tensors in scratch buffers large enough for the raw bond dimensions
+      int64_t maxraw = 1;
+      for (int j = 0; j < N; ++j) maxraw = std::max<int64_t>(maxraw, (int64_t)dims[j] * d * dims[j + 1]);
+      for (int j = 0; j <= N; ++j)
+        if (dims[j] < 1) fail(TDVP_EINVAL, "bond dimensions must be >= 1");
+      std::vector<double2*> raw(N);
+      for (int j = 0; j < N; ++j) {
+        const int64_t n = (int64_t)dims[j] * d * dims[j + 1];
+        raw[j] = dalloc<double2>(std::max<int64_t>(n, (int64_t)d * chi_cap * std::max(dims[j + 1], chi_cap)));
+        CUDA_TRY(cudaMemcpy(raw[j], tensors[j], sizeof(double2) * n, cudaMemcpyHostToDevice));
+      }
+      std::vector<int> rd(dims, dims + N + 1);  // current raw dims
+      int64_t big = 1;
+      for (int j = 0; j < N; ++j) big = std::max<int64_t>(big, (int64_t)std::max(rd[j], chi_cap) * d);
+      for (int j = 0; j <= N; ++j) big = std::max<int64_t>(big, rd[j]);
+      auto* sl = new Slot();
+      std::unique_ptr<Slot> guard(sl);
+      sl->ensure(big * big, 1, 0, big, 1);
+      double2* L = dalloc<double2>(big * big);
+      double2* R = dalloc<double2>(big * big);
+      double* Vt = dalloc<double>(big);
+      // left-to-right: A_j = U, carry Lambda V^dagger into site j+1
+      for (int j = 0; j + 1 < N; ++j) {
+        const int a = rd[j], b = rd[j + 1];
+        const int chi = device_split(S, sl, raw[j], a * d, b, chi_cap, 0.0, eps, L, Vt, R, nullptr, nullptr, s);
+        // A_j = Psi_L V  (= U), stored back in raw[j] as [a][d][chi]
+        ScaleBatch sb{};
+        sb.n = 1;
+        sb.d[0] = ScaleDesc{L, raw[j], Vt, a * d, 1, chi, 0};
+        launch_scale_bond(sb, s);
+        // site j+1 <- (Lambda V^dagger) site j+1
+        const int c = rd[j + 2];
+        ZGemmBatch g{};
+        g.n = 1;
+        g.d[0] = ZGemmDesc{};
+        auto& q = g.d[0];
+        q.M = chi;
+        q.N = d * c;
+        q.K = b;
+        q.A = R;
+        q.a_rs = b;
+        q.a_cs = 1;
+        q.B = raw[j + 1];
+        q.b_rs = (int64_t)d * c;
+        q.b_cs = 1;
+        q.C = sl->theta;
+        q.c_rs = (int64_t)d * c;
+        q.c_cs = 1;
+        launch_zgemm(g, s);
+        CUDA_TRY(cudaMemcpyAsync(raw[j + 1], sl->theta, sizeof(double2) * chi * d * c, cudaMemcpyDeviceToDevice, s));
+        rd[j + 1] = chi;
+      }
+      // normalise: the norm is carried by the last tensor
+      {
+        const int64_t n = (int64_t)rd[N - 1] * d;
+        std::vector<double2> h(n);
+        CUDA_TRY(cudaMemcpy(h.data(), raw[N - 1], sizeof(double2) * n, cudaMemcpyDeviceToHost));
+        double nrm = 0;
+        for (auto& v : h) nrm += v.x * v.x + v.y * v.y;
+        nrm = std::sqrt(nrm);
+        if (!(nrm > 0)) fail(TDVP_ENUMERIC, "initial state has zero norm");
+        for (auto& v : h) v = zscale(v, 1.0 / nrm);
+        CUDA_TRY(cudaMemcpy(raw[N - 1], h.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
+      }
+      // right-to-left: C = U Lambda V^dagger; Psi_j = Lambda V^dagger, V_{j-1} = 1/Lambda
+      for (int j = N - 1; j >= 1; --j) {
+        const int a = rd[j], c = rd[j + 1];
+        const int chi = device_split(S, sl, raw[j], a, d * c, chi_cap, 0.0, eps, L, S->V[j - 1], S->Psi[j],
+                                     nullptr, nullptr, s);
+        S->dims[j - 1] = chi;
+        // site j-1 <- A_{j-1} (U Lambda)
+        const int p = rd[j - 1];
+        ZGemmBatch g{};
+        g.n = 1;
+        g.d[0] = ZGemmDesc{};
+        auto& q = g.d[0];
+        q.M = p * d;
+        q.N = chi;
+        q.K = a;
+        q.A = raw[j - 1];
+        q.a_rs = a;
+        q.a_cs = 1;
+        q.B = L;
+        q.b_rs = chi;
+        q.b_cs = 1;
+        q.C = sl->theta;
+        q.c_rs = chi;
+        q.c_cs = 1;
+        launch_zgemm(g, s);
+        CUDA_TRY(cudaMemcpyAsync(raw[j - 1], sl->theta, sizeof(double2) * p * d * chi, cudaMemcpyDeviceToDevice, s));
+        rd[j] = chi;
+      }
+      CUDA_TRY(cudaMemcpyAsync(S->Psi[0], raw[0], sizeof(double2) * d * rd[1], cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      for (auto p : raw) dfree(p);
+      dfree(L);
+      dfree(R);
+      dfree(Vt);
+    } catch (...) {
+      free_mps(S);
+      throw;
+    }
+    *out = S;
+  });
+}
+
+int tdvp_mps_bond_dims(tdvp_mps mps, int* out) {
+  return ok_or_code([&] {
+    if (!mps || !out) fail(TDVP_EINVAL, "NULL argument");
+    std::memcpy(out, mps->dims.data(), sizeof(int) * (mps->N - 1));
+  });
+}
+
+int tdvp_mps_size(tdvp_mps mps, int* N, int* d) {
+  return ok_or_code([&] {
+    if (!mps) fail(TDVP_EINVAL, "NULL mps");
+    if (N) *N = mps->N;
+    if (d) *d = mps->d;
+  });
+}
+
+int tdvp_mps_get_site(tdvp_mps mps, int j, double* out) {
+  return ok_or_code([&] {
+    if (!mps || !out || j < 0 || j >= mps->N) fail(TDVP_EINVAL, "bad argument");
+    const size_t n = (size_t)mps->chiL(j) * mps->d * mps->chiR(j);
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(out, mps->Psi[j], sizeof(double2) * n, cudaMemcpyDeviceToHost));
+  });
+}
+
+int tdvp_mps_get_bond(tdvp_mps mps, int j, double* out) {
+  return ok_or_code([&] {
+    if (!mps || !out || j < 0 || j >= mps->N - 1) fail(TDVP_EINVAL, "bad argument");
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(out, mps->V[j], sizeof(double) * mps->dims[j], cudaMemcpyDeviceToHost));
+  });
+}
+
+void tdvp_free_mps(tdvp_mps mps) { free_mps(mps); }
+
+int tdvp_step(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps, tdvp_step_stats* stats,
+              void* stream) {
+  return ok_or_code([&] {
+    if (!mps || !mpo) fail(TDVP_EINVAL, "NULL handle");
+    if (n_steps < 0) fail(TDVP_EINVAL, "n_steps < 0");
+    step_impl(mps, mpo, params, n_steps, stats, (cudaStream_t)stream);
+  });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Measurement (transfer matrices, FP64)
+// ---------------------------------------------------------------------------
+namespace {
+
+// rho[s][s'] = sum_{a,b} conj(M[a,s,b]) Y[a,s',b]  (one block per (s, s'))
+__global__ void rho_kernel(const double2* M, const double2* Y, int A, int d, int B, double2* rho) {
+  const int s = blockIdx.x / d, sp = blockIdx.x % d;
+  __shared__ double2 red[256];
+  double2 acc = make_double2(0, 0);
+  for (int64_t i = threadIdx.x; i < (int64_t)A * B; i += blockDim.x) {
+    const int a = (int)(i / B), b = (int)(i % B);
+    zfma_cj(acc, M[((int64_t)a * d + s) * B + b], Y[((int64_t)a * d + sp) * B + b]);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = zadd(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rho[blockIdx.x] = red[0];
+}
+
+ZGemmDesc gemm(int M, int N, int K, const double2* A, int64_t ars, int64_t acs, int ca, const double2* B,
+               int64_t brs, int64_t bcs, double2* C, int64_t crs) {
+  ZGemmDesc q{};
+  q.M = M;
+  q.N = N;
+  q.K = K;
+  q.A = A;
+  q.a_rs = ars;
+  q.a_cs = acs;
+  q.conj_a = ca;
+  q.B = B;
+  q.b_rs = brs;
+  q.b_cs = bcs;
+  q.C = C;
+  q.c_rs = crs;
+  q.c_cs = 1;
+  return q;
+}
+
+void run1(const ZGemmDesc& q, cudaStream_t s) {
+  ZGemmBatch g{};
+  g.n = 1;
+  g.d[0] = q;
+  launch_zgemm(g, s);
+}
+
+struct MeasureBufs {
+  std::vector<double2*> EL, ER;
+  double2* Mj = nullptr;
+  double2* X = nullptr;
+  double2* Y = nullptr;
+  double2* rho = nullptr;
+  ~MeasureBufs() {
+    for (auto p : EL) dfree(p);
+    for (auto p : ER) dfree(p);
+    dfree(Mj);
+    dfree(X);
+    dfree(Y);
+    dfree(rho);
+  }
+};
+
+// M_j = Psi_j V_j (V_j omitted on the last site) into dst
+void site_matrix(tdvp_mps_s* S, int j, double2* dst, cudaStream_t s) {
+  const int A = S->chiL(j), B = S->chiR(j), d = S->d;
+  if (j == S->N - 1) {
+    CUDA_TRY(cudaMemcpyAsync(dst, S->Psi[j], sizeof(double2) * A * d * B, cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  ScaleBatch sb{};
+  sb.n = 1;
+  sb.d[0] = ScaleDesc{S->Psi[j], dst, S->V[j], A, d, B, 0};
+  launch_scale_bond(sb, s);
+}
+
+// left transfer: E'[b][b'] = sum conj(Ma[a,s,b]) E[a,a'] Mb[a',s,b']
+void transfer_left(const double2* E, const double2* Ma, const double2* Mb, int Aa, int Ab, int d, int Ba, int Bb,
+                   double2* X, double2* out, cudaStream_t s) {
+  run1(gemm(Aa, d * Bb, Ab, E, Ab, 1, 0, Mb, (int64_t)d * Bb, 1, X, (int64_t)d * Bb), s);
+  run1(gemm(Ba, Bb, Aa * d, Ma, 1, Ba, 1, X, Bb, 1, out, Bb), s);
+}
+
+void measure_impl(tdvp_mps_s* S, const double2 op[4], double* out, bool want_local, double* norm_out) {
+  cudaStream_t s = 0;
+  const int N = S->N, d = S->d;
+  MeasureBufs mb;
+  const int64_t big = (int64_t)S->chi_cap * d * S->chi_cap;
+  mb.Mj = dalloc<double2>(big);
+  mb.X = dalloc<double2>(big);
+  mb.Y = dalloc<double2>(big);
+  mb.rho = dalloc<double2>(16);
+  mb.EL.resize(N + 1);
+  for (int j = 0; j <= N; ++j) {
+    const int c = j == 0 ? 1 : S->chiR(j - 1);
+    mb.EL[j] = dalloc<double2>((size_t)c * c);
+  }
+  const double2 one = make_double2(1, 0);
+  CUDA_TRY(cudaMemcpy(mb.EL[0], &one, sizeof(double2), cudaMemcpyHostToDevice));
+  for (int j = 0; j < N; ++j) {
+    site_matrix(S, j, mb.Mj, s);
+    const int A = S->chiL(j), B = S->chiR(j);
+    transfer_left(mb.EL[j], mb.Mj, mb.Mj, A, A, d, B, B, mb.X, mb.EL[j + 1], s);
+  }
+  double2 nrm;
+  CUDA_TRY(cudaMemcpy(&nrm, mb.EL[N], sizeof(double2), cudaMemcpyDeviceToHost));
+  if (norm_out) *norm_out = nrm.x;
+  if (!want_local) return;
+  if (!(nrm.x > 0)) fail(TDVP_ENUMERIC, "state has zero norm");
+  mb.ER.resize(N);
+  for (int j = 0; j < N; ++j) {
+    const int c = S->chiR(j);
+    mb.ER[j] = dalloc<double2>((size_t)c * c);
+  }
+  CUDA_TRY(cudaMemcpy(mb.ER[N - 1], &one, sizeof(double2), cudaMemcpyHostToDevice));
+  for (int j = N - 1; j >= 1; --j) {
+    site_matrix(S, j, mb.Mj, s);
+    const int A = S->chiL(j), B = S->chiR(j);
+    // Y[(a' s)][b] = sum_b' M[(a' s)][b'] E_R[b][b']
+    run1(gemm(A * d, B, B, mb.Mj, B, 1, 0, mb.ER[j], 1, B, mb.Y, B), s);
+    // E'[a][a'] = sum_(s b) conj(M[a][(s b)]) Y[a'][(s b)]
+    run1(gemm(A, A, d * B, mb.Mj, (int64_t)d * B, 1, 1, mb.Y, 1, (int64_t)d * B, mb.ER[j - 1], A), s);
+  }
+  std::vector<double2> rho(d * d);
+  for (int j = 0; j < N; ++j) {
+    site_matrix(S, j, mb.Mj, s);
+    const int A = S->chiL(j), B = S->chiR(j);
+    run1(gemm(A, d * B, A, mb.EL[j], A, 1, 0, mb.Mj, (int64_t)d * B, 1, mb.X, (int64_t)d * B), s);
+    run1(gemm(A * d, B, B, mb.X, B, 1, 0, mb.ER[j], 1, B, mb.Y, B), s);
+    rho_kernel<<<d * d, 256, 0, s>>>(mb.Mj, mb.Y, A, d, B, mb.rho);
+    LAUNCH_CHECK();
+    CUDA_TRY(cudaMemcpy(rho.data(), mb.rho, sizeof(double2) * d * d, cudaMemcpyDeviceToHost));
+    double v = 0;
+    for (int q = 0; q < d * d; ++q) v += rho[q].x * op[q].x - rho[q].y * op[q].y;
+    out[j] = v / nrm.x;
+  }
+}
+
+// temporary workspace for the kernel-level entry points
+struct OpCtx {
+  Slot slot;
+  int* d_status = nullptr;
+  int* d_flag = nullptr;
+  int* d_chi = nullptr;
+  double* d_w = nullptr;
+  int* h_flag = nullptr;
+  OpCtx() {
+    d_status = dalloc<int>(1);
+    d_flag = dalloc<int>(1);
+    d_chi = dalloc<int>(1);
+    d_w = dalloc<double>(1);
+    CUDA_TRY(cudaMemset(d_status, 0, sizeof(int)));
+    CUDA_TRY(cudaMallocHost((void**)&h_flag, sizeof(int)));
+  }
+  ~OpCtx() {
+    dfree(d_status);
+    dfree(d_flag);
+    dfree(d_chi);
+    dfree(d_w);
+    if (h_flag) cudaFreeHost(h_flag);
+  }
+  void check(cudaStream_t s) {
+    int st = 0;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaMemcpy(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 1) fail(TDVP_ETIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
+    if (st & (2 | 8)) fail(TDVP_ENUMERIC, "NaN or zero norm");
+    if (st & 4) fail(TDVP_ENUMERIC, "tridiagonal eigen-solver did not converge");
+  }
+};
+
+void check_op_dims(int precision, int nsite, int chi_l, int chi_r, int m, int d) {
+  if (precision < TDVP_FP64 || precision > TDVP_TF32X3) fail(TDVP_EINVAL, "invalid precision");
+  if ((nsite != 1 && nsite != 2) || chi_l < 1 || chi_r < 1 || m < 1 || d < 2 || d > 4 || chi_l > 4096 ||
+      chi_r > 4096)
+    fail(TDVP_EINVAL, "invalid dimensions");
+  if (precision != TDVP_FP64 && !tc_available()) fail(TDVP_ECUDA, "tensor-core path unavailable");
+  require_device();
+}
+
+// H_eff problem on caller buffers; the sparse MPO is built from host W
+struct OpHeff {
+  DeviceWOp wop;
+  MvProb prob{};
+  void setup(OpCtx& C, int precision, int nsite, int chi_l, int chi_r, int m, int d, const double* W,
+             const double* L, const double* R, int kmax, cudaStream_t s) {
+    std::vector<double2> Wd((const double2*)W, (const double2*)W + (size_t)m * m * d * d);
+    const int D = nsite == 2 ? d * d : d;
+    if (nsite == 2) wop.build(two_site_mpo(Wd, m, d), m, D, false);
+    else wop.build(Wd, m, D, false);
+    const int c = std::max(chi_l, chi_r);
+    C.slot.ensure((int64_t)chi_l * D * chi_r, (int64_t)chi_l * m * D * chi_r,
+                  precision == TDVP_FP64 ? 0 : mixed_cap_floats(c, m, d), std::max<int64_t>(1, (int64_t)c * d),
+                  kmax);
+    prob.A = chi_l;
+    prob.B = chi_r;
+    prob.D = D;
+    prob.m = m;
+    prob.L = (const double2*)L;
+    prob.R = (const double2*)R;
+    prob.W = wop.op();
+    prob.slot = &C.slot;
+    if (precision != TDVP_FP64) {
+      const bool x3 = precision == TDVP_TF32X3;
+      prep_L_forms({EnvFormJob{prob.L, chi_l, m, C.slot.f[5], x3 ? C.slot.f[6] : nullptr}}, s);
+      prep_R_forms({EnvFormJob{prob.R, chi_r, m, C.slot.f[7], x3 ? C.slot.f[8] : nullptr}}, s);
+      prob.L32[0] = C.slot.f[5];
+      prob.L32[1] = x3 ? C.slot.f[6] : nullptr;
+      prob.R32[0] = C.slot.f[7];
+      prob.R32[1] = x3 ? C.slot.f[8] : nullptr;
+      prob.ldL = pad4(2 * (int64_t)chi_l);
+      prob.ldR = pad4(2 * (int64_t)m * chi_r);
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int tdvp_norm(tdvp_mps mps, double* out) {
+  return ok_or_code([&] {
+    if (!mps || !out) fail(TDVP_EINVAL, "NULL argument");
+    CUDA_TRY(cudaDeviceSynchronize());
+    const double2 I2[4] = {make_double2(1, 0), make_double2(0, 0), make_double2(0, 0), make_double2(1, 0)};
+    measure_impl(mps, I2, nullptr, false, out);
+  });
+}
+
+int tdvp_measure(tdvp_mps mps, int obs, double* out) {
+  return ok_or_code([&] {
+    if (!mps || !out) fail(TDVP_EINVAL, "NULL argument");
+    if (mps->d != 2) fail(TDVP_EINVAL, "Pauli observables need d = 2");
+    double2 op[4];
+    const double2 Z = make_double2(0, 0), One = make_double2(1, 0);
+    if (obs == TDVP_OBS_SZ) {
+      op[0] = One; op[1] = Z; op[2] = Z; op[3] = make_double2(-1, 0);
+    } else if (obs == TDVP_OBS_SX) {
+      op[0] = Z; op[1] = One; op[2] = One; op[3] = Z;
+    } else if (obs == TDVP_OBS_SY) {
+      op[0] = Z; op[1] = make_double2(0, -1); op[2] = make_double2(0, 1); op[3] = Z;
+    } else {
+      fail(TDVP_EINVAL, "unknown observable");
+    }
+    // the reduced density matrix is rho[s][s'] ~ <s'|rho_j|s>^*: <O> = sum rho[s][s'] O[s][s']
+    CUDA_TRY(cudaDeviceSynchronize());
+    measure_impl(mps, op, out, true, nullptr);
+  });
+}
+
+int tdvp_energy(tdvp_mps mps, tdvp_mpo mpo, double* out) {
+  return ok_or_code([&] {
+    if (!mps || !mpo || !out) fail(TDVP_EINVAL, "NULL argument");
+    if (mpo->N != mps->N) fail(TDVP_EINVAL, "MPO and MPS have different N");
+    CUDA_TRY(cudaDeviceSynchronize());
+    cudaStream_t s = 0;
+    ensure_small_buffers(mps);
+    const int N = mps->N, m = mpo->m, d = mps->d;
+    Slot* sl = slot_for(mps, 0, m, 1);
+    const int64_t big = (int64_t)mps->chi_cap * mps->chi_cap * m;
+    double2* E0 = dalloc<double2>(big);
+    double2* E1 = dalloc<double2>(big);
+    std::unique_ptr<double2, void (*)(double2*)> g0(E0, [](double2* p) { dfree(p); });
+    std::unique_ptr<double2, void (*)(double2*)> g1(E1, [](double2* p) { dfree(p); });
+    std::vector<double2> bl(m, make_double2(0, 0));
+    bl[m - 1] = make_double2(1, 0);
+    CUDA_TRY(cudaMemcpy(E0, bl.data(), sizeof(double2) * m, cudaMemcpyHostToDevice));
+    Ctx c{s, mps->d_status, TDVP_FP64};
+    for (int j = 0; j < N; ++j) {
+      site_matrix(mps, j, sl->Amat, s);
+      env_batch(0, {EnvProb{mps->chiL(j), mps->chiR(j), d, m, E0, sl->Amat, E1, mpo->w1.op(), sl}}, c);
+      std::swap(E0, E1);
+    }
+    std::vector<double2> fin(m);
+    CUDA_TRY(cudaMemcpy(fin.data(), E0, sizeof(double2) * m, cudaMemcpyDeviceToHost));
+    double nrm = 0;
+    const double2 I2[4] = {make_double2(1, 0), make_double2(0, 0), make_double2(0, 0), make_double2(1, 0)};
+    measure_impl(mps, I2, nullptr, false, &nrm);
+    if (!(nrm > 0)) fail(TDVP_ENUMERIC, "state has zero norm");
+    g0.release();
+    g1.release();
+    dfree(E0);
+    dfree(E1);
+    *out = fin[0].x / nrm;
+  });
+}
+
+int tdvp_overlap(tdvp_mps a, tdvp_mps b, double* out) {
+  return ok_or_code([&] {
+    if (!a || !b || !out) fail(TDVP_EINVAL, "NULL argument");
+    if (a->N != b->N || a->d != b->d) fail(TDVP_EINVAL, "states of different shape");
+    CUDA_TRY(cudaDeviceSynchronize());
+    cudaStream_t s = 0;
+    const int N = a->N, d = a->d;
+    const int64_t big = (int64_t)std::max(a->chi_cap, b->chi_cap) * d * std::max(a->chi_cap, b->chi_cap);
+    MeasureBufs mb;
+    mb.Mj = dalloc<double2>(big);
+    mb.Y = dalloc<double2>(big);
+    mb.X = dalloc<double2>(big);
+    double2* E0 = dalloc<double2>(big);
+    double2* E1 = dalloc<double2>(big);
+    mb.EL = {E0, E1};
+    const double2 one = make_double2(1, 0);
+    CUDA_TRY(cudaMemcpy(E0, &one, sizeof(double2), cudaMemcpyHostToDevice));
+    for (int j = 0; j < N; ++j) {
+      site_matrix(a, j, mb.Mj, s);
+      site_matrix(b, j, mb.Y, s);
+      transfer_left(E0, mb.Mj, mb.Y, a->chiL(j), b->chiL(j), d, a->chiR(j), b->chiR(j), mb.X, E1, s);
+      std::swap(E0, E1);
+    }
+    double2 r;
+    CUDA_TRY(cudaMemcpy(&r, E0, sizeof(double2), cudaMemcpyDeviceToHost));
+    out[0] = r.x;
+    out[1] = r.y;
+  });
+}
+
+int tdvp_op_heff(int precision, int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,
+                 const double* R, const double* x, double* y, void* stream) {
+  return ok_or_code([&] {
+    if (!W || !L || !R || !x || !y) fail(TDVP_EINVAL, "NULL argument");
+    check_op_dims(precision, nsite, chi_l, chi_r, m, d);
+    cudaStream_t s = (cudaStream_t)stream;
+    OpCtx C;
+    OpHeff H;
+    H.setup(C, precision, nsite, chi_l, chi_r, m, d, W, L, R, 1, s);
+    Ctx c{s, C.d_status, precision};
+    matvec_batch({H.prob}, {(const double2*)x}, {(double2*)y}, c);
+    C.check(s);
+  });
+}
+
+int tdvp_op_expm(int precision, int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,
+                 const double* R, const double* x, double* y, double t, int kmax, double tol, int* n_vectors,
+                 void* stream) {
+  return ok_or_code([&] {
+    if (!W || !L || !R || !x || !y) fail(TDVP_EINVAL, "NULL argument");
+    if (kmax < 1 || kmax > KRYLOV_MAX || tol < 0) fail(TDVP_EINVAL, "invalid Krylov settings");
+    check_op_dims(precision, nsite, chi_l, chi_r, m, d);
+    cudaStream_t s = (cudaStream_t)stream;
+    OpCtx C;
+    OpHeff H;
+    H.setup(C, precision, nsite, chi_l, chi_r, m, d, W, L, R, kmax, s);
+    Ctx c{s, C.d_status, precision};
+    expm_batch({H.prob}, {(const double2*)x}, {(double2*)y}, {t}, kmax, tol, c);
+    C.check(s);
+    if (n_vectors) {
+      LzState st;
+      CUDA_TRY(cudaMemcpy(&st, C.slot.st, sizeof(LzState), cudaMemcpyDeviceToHost));
+      *n_vectors = st.nvec_used;
+    }
+  });
+}
+
+int tdvp_op_env(int precision, int side, int chi_l, int chi_r, int m, int d, const double* W, const double* env,
+                const double* A, double* out, void* stream) {
+  return ok_or_code([&] {
+    if (!W || !env || !A || !out) fail(TDVP_EINVAL, "NULL argument");
+    if (side != 0 && side != 1) fail(TDVP_EINVAL, "side must be 0 or 1");
+    check_op_dims(precision, 1, chi_l, chi_r, m, d);
+    cudaStream_t s = (cudaStream_t)stream;
+    OpCtx C;
+    DeviceWOp wop;
+    std::vector<double2> Wd((const double2*)W, (const double2*)W + (size_t)m * m * d * d);
+    wop.build(Wd, m, d, side == 1);
+    const int c = std::max(chi_l, chi_r);
+    C.slot.ensure((int64_t)chi_l * d * chi_r, (int64_t)c * m * d * c,
+                  precision == TDVP_FP64 ? 0 : mixed_cap_floats(c, m, d), (int64_t)c * d, 1);
+    Ctx cx{s, C.d_status, precision};
+    env_batch(side, {EnvProb{chi_l, chi_r, d, m, (const double2*)env, (const double2*)A, (double2*)out, wop.op(),
+                             &C.slot}},
+              cx);
+    C.check(s);
+  });
+}
+
+int tdvp_op_split(int rows, int cols, const double* theta, int chi_max, double w_max, double eps, double* Psi_L,
+                  double* V, double* Psi_R, double* s_out, int* chi, double* w, void* stream) {
+  return ok_or_code([&] {
+    if (!theta || !Psi_L || !V || !Psi_R || !chi || !w) fail(TDVP_EINVAL, "NULL argument");
+    if (rows < 1 || cols < 1 || rows > 4096 || cols > 4096 || chi_max < 1 || w_max < 0 || eps < 0)
+      fail(TDVP_EINVAL, "invalid arguments");
+    require_device();
+    cudaStream_t s = (cudaStream_t)stream;
+    OpCtx C;
+    const int64_t nv = std::min(rows, cols), len = std::max(rows, cols);
+    C.slot.ensure(nv * len, 1, 0, nv, 1);
+    // the Acc buffer must hold nv*nv and X nv*len: both <= cap_vec = max(nv*len, nv*nv)
+    SvdBatch sb{};
+    sb.n = 1;
+    sb.status = C.d_status;
+    SvdDesc& q = sb.d[0];
+    q = SvdDesc{};
+    q.theta = (const double2*)theta;
+    q.rows = rows;
+    q.cols = cols;
+    q.X = C.slot.svdX;
+    q.Acc = C.slot.svdAcc;
+    q.sig = C.slot.sig;
+    q.perm = C.slot.perm;
+    q.rotated = C.slot.rot;
+    q.conv = C.slot.conv;
+    q.chi_max = chi_max;
+    q.w_max = w_max;
+    q.eps = eps;
+    q.chi = C.d_chi;
+    q.w = C.d_w;
+    q.PsiL = (double2*)Psi_L;
+    q.V = V;
+    q.PsiR = (double2*)Psi_R;
+    q.s_sorted = s_out;
+    svd_split(sb, C.d_flag, C.h_flag, s);
+    C.check(s);
+    CUDA_TRY(cudaMemcpy(chi, C.d_chi, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(w, C.d_w, sizeof(double), cudaMemcpyDeviceToHost));
+  });
+}
+
+int tdvp_schedule(int N, int n_seg, const int* seg_len, int merge_turning, int half, int* out, int max_ops) {
+  int count = 0;
+  int rc = ok_or_code([&] {
+    if (half != 1 && half != 2) fail(TDVP_EINVAL, "half must be 1 or 2");
+    std::vector<int> seg;
+    if (n_seg <= 1 || !seg_len) seg = {N};
+    else seg.assign(seg_len, seg_len + n_seg);
+    if (N < 2) fail(TDVP_EINVAL, "need N >= 2");
+    std::vector<SchedOp> ops;
+    build_half(N, seg, half, merge_turning, ops);
+    count = (int)ops.size();
+    if (out) {
+      if (max_ops < count) fail(TDVP_EINVAL, "output too small");
+      for (int i = 0; i < count; ++i) {
+        const SchedOp& o = ops[i];
+        int* r = out + 7 * i;
+        r[0] = o.seg;
+        r[1] = o.kind;
+        r[2] = o.j;
+        r[3] = o.tfac;
+        r[4] = o.env;
+        r[5] = o.boundary;
+        r[6] = o.stage;
+      }
+    }
+  });
+  return rc == TDVP_OK ? count : rc;
+}
+
+int tdvp_tridiag_expm(int k, const double* alpha, const double* beta, double t, double* c_out) {
+  return ok_or_code([&] {
+    if (k < 1 || k > KRYLOV_MAX || !alpha || !c_out || (k > 1 && !beta)) fail(TDVP_EINVAL, "bad argument");
+    std::vector<double> work(2 * k * k);
+    std::vector<double2> c(k);
+    if (tridiag_expm_e0(k, alpha, beta, t, c.data(), work.data()) < 0)
+      fail(TDVP_ENUMERIC, "tridiagonal eigen-solver did not converge");
+    std::memcpy(c_out, c.data(), sizeof(double2) * k);
+  });
+}
+
+int tdvp_profile(int enable) {
+  return ok_or_code([&] {
+    CUDA_TRY(cudaDeviceSynchronize());
+    prof_enable(enable != 0);
+  });
+}
+
+int tdvp_profile_read(int idx, char* name, int name_len, double* ms, int64_t* launches, double* flops,
+                      double* bytes) {
+  int n = 0;
+  int rc = ok_or_code([&] {
+    std::string nm;
+    double t = 0, f = 0, b = 0;
+    int64_t l = 0;
+    if (idx < 0) {
+      n = prof_read(-1, nm, t, l, f, b);
+      return;
+    }
+    if (!prof_read(idx, nm, t, l, f, b)) fail(TDVP_EINVAL, "profile index out of range");
+    if (name && name_len > 0) {
+      std::strncpy(name, nm.c_str(), name_len - 1);
+      name[name_len - 1] = 0;
+    }
+    if (ms) *ms = t;
+    if (launches) *launches = l;
+    if (flops) *flops = f;
+    if (bytes) *bytes = b;
+    n = 1;
+  });
+  return rc == TDVP_OK ? n : rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// Internal declarations shared by the translation units of libtdvp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "tdvp.h"
+
+namespace tdvp {
+
+// ---------------------------------------------------------------------------
+// Errors: internal code throws TdvpError; the C ABI converts it to a code.
+// ---------------------------------------------------------------------------
+struct TdvpError {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what, const char* file, int line);
+#define CUDA_TRY(x) ::tdvp::cuda_check((x), #x, __FILE__, __LINE__)
+#define LAUNCH_CHECK() ::tdvp::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// Global counter of kernels launched (for the statistics only).
+extern int64_t g_launches;
+
+// Optional per-kernel timing with CUDA events recorded on the launching
+// stream around each launch (enabled by tdvp_profile). `flops` and `bytes`
+// are the algorithmic work of the launch.
+extern bool g_prof_on;
+struct ProfScope {
+  int slot = -1;
+  cudaStream_t s = 0;
+  ProfScope(const char* name, cudaStream_t s, double flops, double bytes);
+  ~ProfScope();
+};
+void prof_enable(bool on);
+int prof_read(int idx, std::string& name, double& ms, int64_t& launches, double& flops, double& bytes);
+
+// ---------------------------------------------------------------------------
+// Complex helpers (double2 / float2 hold re, im)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// a += b * c
+__host__ __device__ inline void zfma(double2& a, double2 b, double2 c) {
+  a.x = fma(b.x, c.x, a.x);
+  a.x = fma(-b.y, c.y, a.x);
+  a.y = fma(b.x, c.y, a.y);
+  a.y = fma(b.y, c.x, a.y);
+}
+// a += conj(b) * c
+__host__ __device__ inline void zfma_cj(double2& a, double2 b, double2 c) {
+  a.x = fma(b.x, c.x, a.x);
+  a.x = fma(b.y, c.y, a.x);
+  a.y = fma(b.x, c.y, a.y);
+  a.y = fma(-b.y, c.x, a.y);
+}
+__host__ __device__ inline void cfma(float2& a, float2 b, float2 c) {
+  a.x = fmaf(b.x, c.x, a.x);
+  a.x = fmaf(-b.y, c.y, a.x);
+  a.y = fmaf(b.x, c.y, a.y);
+  a.y = fmaf(b.y, c.x, a.y);
+}
+
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+constexpr int MAXB = 32;        // largest batch of local problems in one launch
+constexpr int KRYLOV_MAX = 24;  // largest Krylov dimension
+
+// ---------------------------------------------------------------------------
+// FP64 complex GEMM (SIMT), batched. op(A)(i,k) = A[i*a_rs + k*a_cs] (conj if
+// conj_a, times kscale[k] if given); B(k,j) = B[k*b_rs + j*b_cs]; C(i,j) at
+// C[i*c_rs + j*c_cs]; C = op(A) op(B) (+ C if accumulate).
+// ---------------------------------------------------------------------------
+struct ZGemmDesc {
+  int M, N, K;
+  int conj_a, conj_b, accumulate;
+  const int* skip;        // optional: nonzero -> problem skipped
+  const double2* A;
+  const double2* B;
+  double2* C;
+  const double* kscale;
+  int64_t a_rs, a_cs, b_rs, b_cs, c_rs, c_cs;
+};
+struct ZGemmBatch {
+  int n;
+  ZGemmDesc d[MAXB];
+};
+void launch_zgemm(const ZGemmBatch& b, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Sparse MPO operator applied in the "W stage" of a contraction:
+// Y[a, w', S, b] = sum_{w, S'} Wop[w, w', S, S'] X[a, w, S', b]
+// Blocks are grouped by w' (CSR over w'): blocks col_ptr[w']..col_ptr[w'+1]-1
+// have w_left = row_idx[blk] and values blk64/blk32 [D][D] (S_out, S_in).
+// ---------------------------------------------------------------------------
+struct WOp {
+  int m, D, nnz;
+  const int* col_ptr;
+  const int* row_idx;
+  const double2* blk64;
+  const float2* blk32;
+};
+template <typename T>
+struct WStageDesc {
+  int A, B;
+  const int* skip;
+  const T* X;
+  int64_t x_a, x_w, x_s, x_b;
+  T* Y;         // output (fp64 complex or fp32 complex)
+  T* Ylo;       // fp32 only: optional second output holding x - tf32(x) (3xTF32 operands)
+  int64_t y_a, y_w, y_s, y_b;
+  WOp W;
+};
+template <typename T>
+struct WStageBatch {
+  int n;
+  int round_tf32;  // fp32 only: round outputs to tf32 (and write Ylo residuals)
+  WStageDesc<T> d[MAXB];
+};
+void launch_wstage(const WStageBatch<double2>& b, cudaStream_t s);
+void launch_wstage(const WStageBatch<float2>& b, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Small elementwise kernels
+// ---------------------------------------------------------------------------
+// dst[i, s, j] = src[i, s, j] * (left ? v[i] : v[j]) for a [rows][d][cols] tensor
+struct ScaleDesc {
+  const double2* src;
+  double2* dst;
+  const double* v;
+  int rows, d, cols, left;
+};
+struct ScaleBatch {
+  int n;
+  ScaleDesc d[MAXB];
+};
+void launch_scale_bond(const ScaleBatch& b, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Operand preparation for the tensor-core path.
+//  A form: fp32 complex [M][K] row-major, row pitch lda (floats), from an
+//          FP64 complex source with element (i,k) at src[i*rs + k*cs].
+//  B form: the real embedding of a complex B (N x K, element (n,k) at
+//          src[n*rs + k*cs]) as fp32 [2N][2K] rows, pitch ldb (floats):
+//          row 2n = (Re b, -Im b) pairs, row 2n+1 = (Im b, Re b) pairs, so that
+//          [A_re A_im ...] . row gives Re / Im of sum_k a_k b_k.
+//  hi = tf32(x), lo = tf32(x - hi) when lo != nullptr; conj applies to src.
+// ---------------------------------------------------------------------------
+struct PrepDesc {
+  const int* skip;
+  const double2* src;
+  const float2* src32;  // alternative fp32 complex source (src == nullptr)
+  int64_t rs, cs;
+  int rows, cols;     // complex rows (M or N) and complex K
+  int conj;
+  float* hi;
+  float* lo;
+  int64_t ld;         // row pitch of the destination in floats
+  int embed;          // 0: A form, 1: B form
+};
+struct PrepBatch {
+  int n;
+  PrepDesc d[MAXB];
+};
+void launch_prep(const PrepBatch& b, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Tensor-core (tcgen05, kind::tf32) real GEMM, batched:
+// C[M][N] = sum_pass A_pass[M][K] B_pass[N][K]^T, operands K-major fp32 in
+// global memory, staged by TMA (128B swizzle) into shared memory,
+// accumulated in TMEM (FP32). passes = 1 (A_hi B_hi) or 3 (+ A_hi B_lo + A_lo B_hi).
+// Output: fp32 (c_fp64 = 0) or fp64 (c_fp64 = 1), row pitch ldc elements.
+// ---------------------------------------------------------------------------
+struct TcOperand {
+  const float* hi;
+  const float* lo;
+  int rows, k;        // logical rows and K (floats)
+  int64_t ld;         // row pitch in floats (multiple of 4)
+};
+struct TcProblem {
+  const int* skip;
+  TcOperand A, B;
+  int M, N, K;
+  void* C;
+  int64_t ldc;
+  int c_fp64;
+};
+void launch_tc_gemm(const std::vector<TcProblem>& probs, int passes, int* d_status, cudaStream_t s);
+bool tc_available();
+
+// ---------------------------------------------------------------------------
+// Lanczos exponentiation, batched. Each problem evolves x (length n) by
+// exp(-i t H) with H applied by a callback that runs one batched matvec.
+// ---------------------------------------------------------------------------
+struct LzState {
+  double alpha[KRYLOV_MAX];
+  double beta[KRYLOV_MAX];
+  double2 h[KRYLOV_MAX];
+  double2 g[KRYLOV_MAX];
+  double2 c[KRYLOV_MAX];
+  double beta0;
+  double t;
+  double tol;
+  double err;
+  int k;         // vectors in the basis so far
+  int done;      // 1 = converged / breakdown / zero vector
+  int kmax;
+  int nvec_used;
+};
+
+// ---------------------------------------------------------------------------
+// Host numerics (host_numerics.cpp)
+// ---------------------------------------------------------------------------
+void host_fit_power_law(double alpha, int n_exp, int r_max, std::vector<double2>& x,
+                        std::vector<double2>& lam);
+// c = exp(-i t T) e_0 for symmetric tridiagonal T (alpha diag, beta off-diag)
+__host__ __device__ int tridiag_expm_e0(int k, const double* alpha, const double* beta, double t,
+                                        double2* c, double* work);
+
+// Sweep schedule (schedule.cpp)
+struct SchedOp {
+  int seg, kind;      // kind 0 = fwd2 (pair j, j+1), 1 = back1 (site j)
+  int j, tfac, env;   // env bit 1 = build beta_{j+1}, bit 2 = build gamma_j
+  int boundary, stage;
+};
+void build_half(int N, const std::vector<int>& seg_len, int half, int merge, std::vector<SchedOp>& ops);
+
+}  // namespace tdvp

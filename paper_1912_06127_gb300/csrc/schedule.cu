@@ -1,0 +1,118 @@
+// Sweep schedule of one time step: the serial two-site sweep (Sec. III A,
+// Fig. 2, App. A) and the Stoudenmire-White segment scheme (Sec. III B,
+// Figs. 6-7, App. B). The activity diagrams of App. B are not available as
+// text, so the rules are a reading of the prose:
+//   * segment k sweeps right in the first half iff k and p/2 have the same
+//     parity (the central pair sweeps away from the centre, neighbours
+//     alternate); all directions reverse in the second half;
+//   * the pair straddling a boundary is updated by the left segment (Sec. III B),
+//     which builds both environments next to the boundary afterwards;
+//   * turning pairs where the first half ends (a chain end, or a boundary
+//     where two sweeps meet) are evolved once by dt when merging is on
+//     (App. A); pairs where the first half starts get dt/2 at the start of
+//     the first half and dt/2 at the end of the second;
+//   * a segment leaving a boundary starts with the one-site step of its
+//     boundary site; otherwise two-site and one-site steps alternate as in
+//     the serial sweep.
+// Ops get stages as soon as their segment's previous op and any
+// cross-segment wait allow; one stage runs as one batched launch sequence.
+#include <algorithm>
+#include <map>
+
+#include "common.h"
+
+namespace tdvp {
+
+static bool right_first(int k, int p) { return (k % 2) == ((p / 2) % 2); }
+
+void build_half(int N, const std::vector<int>& seg_len, int half, int merge,
+                std::vector<SchedOp>& out) {
+  const int p = (int)seg_len.size();
+  std::vector<std::pair<int, int>> b(p);
+  int s0 = 0;
+  for (int k = 0; k < p; ++k) {
+    if (seg_len[k] < 2) fail(TDVP_EINVAL, "every segment needs at least two sites");
+    b[k] = {s0, s0 + seg_len[k] - 1};
+    s0 += seg_len[k];
+  }
+  if (s0 != N) fail(TDVP_EINVAL, "segment lengths do not add up to N");
+  const int turn = (half == 1 && merge) ? 2 : 1;
+  const int ENV_L = 1, ENV_R = 2;
+  std::vector<std::vector<SchedOp>> q(p);
+  std::map<int, int> start_boundary;  // seg -> index of its start-of-half boundary op
+  std::map<int, int> end_boundary;    // seg -> index of its end-of-half boundary op
+  auto fwd = [](int k, int j, int tf, int env, int bnd) { return SchedOp{k, 0, j, tf, env, bnd, -1}; };
+  auto bck = [](int k, int j) { return SchedOp{k, 1, j, 1, 0, 0, -1}; };
+  for (int k = 0; k < p; ++k) {
+    const int s = b[k].first, e = b[k].second;
+    bool right = right_first(k, p);
+    if (half == 2) right = !right;
+    auto& Q = q[k];
+    if (right) {
+      int first_back;
+      if (s == 0) {
+        if (half == 1 || !merge) Q.push_back(fwd(k, 0, 1, ENV_L, 0));
+        first_back = 1;
+      } else {
+        first_back = s;
+      }
+      for (int j = first_back; j < e; ++j) {
+        Q.push_back(bck(k, j));
+        bool last = (j == e - 1) && (e == N - 1);
+        Q.push_back(fwd(k, j, last ? turn : 1, last ? ENV_R : ENV_L, 0));
+      }
+      if (e < N - 1) {
+        Q.push_back(bck(k, e));
+        Q.push_back(fwd(k, e, turn, ENV_L | ENV_R, 1));
+        end_boundary[k] = (int)Q.size() - 1;
+      }
+    } else {
+      int first_back;
+      if (e == N - 1) {
+        if (half == 1 || !merge) Q.push_back(fwd(k, N - 2, 1, ENV_R, 0));
+        first_back = N - 2;
+      } else {
+        if (half == 1 || !merge) {
+          Q.push_back(fwd(k, e, 1, ENV_L | ENV_R, 1));
+          start_boundary[k] = (int)Q.size() - 1;
+        }
+        first_back = e;
+      }
+      for (int j = first_back; j > s; --j) {
+        Q.push_back(bck(k, j));
+        bool last = (j - 1 == s) && (s == 0);
+        Q.push_back(fwd(k, j - 1, last ? turn : 1, last ? ENV_L : ENV_R, 0));
+      }
+      if (s > 0) Q.push_back(bck(k, s));
+    }
+  }
+  // as-soon-as-possible stages, iterated to a fixed point
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int k = 0; k < p; ++k) {
+      int prev = -1;
+      for (size_t i = 0; i < q[k].size(); ++i) {
+        int st = prev + 1;
+        if (i == 0 && start_boundary.count(k - 1))
+          st = std::max(st, q[k - 1][start_boundary[k - 1]].stage + 1);
+        auto eb = end_boundary.find(k);
+        if (eb != end_boundary.end() && (int)i == eb->second)
+          st = std::max(st, q[k + 1].back().stage + 1);
+        if (st != q[k][i].stage) {
+          q[k][i].stage = st;
+          changed = true;
+        }
+        prev = q[k][i].stage;
+      }
+    }
+  }
+  out.clear();
+  for (int k = 0; k < p; ++k)
+    for (auto& o : q[k]) out.push_back(o);
+  std::stable_sort(out.begin(), out.end(), [](const SchedOp& a, const SchedOp& c) {
+    return a.stage != c.stage ? a.stage < c.stage : a.seg < c.seg;
+  });
+}
+
+}  // namespace tdvp

@@ -1,0 +1,121 @@
+"""CPU tests of libtdvp: it loads, exports every symbol of include/tdvp.h, and
+its host logic (coupling fit, sweep schedule, tridiagonal exponential) agrees
+with the oracle and with scipy. No kernel runs here."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import models
+from oracle import tdvp as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tdvp():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_06127_gb300 import tdvp as b
+    b.lib()
+    return b
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "tdvp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tdvp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(tdvp):
+    import ctypes
+    L = ctypes.CDLL(tdvp.LIB_PATH)
+    syms = declared_symbols()
+    assert len(syms) >= 25
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_no_cpu_fallback_without_gpu(tdvp):
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("a GPU is present")
+    assert not tdvp.device_ok()
+    with pytest.raises(tdvp.TdvpError) as e:
+        tdvp.init_mps(4, [0, 0, 0, 0], 4)
+    assert e.value.code == -3
+
+
+@pytest.mark.parametrize("alpha,K,rmax", [(3.0, 4, 9), (1.5, 6, 50), (1.5, 8, 100), (2.0, 10, 200),
+                                          (0.75, 6, 40)])
+def test_fit_matches_oracle_fit(tdvp, alpha, K, rmax):
+    x, lam = tdvp.fit_power_law(alpha, K, rmax)
+    xo, lo = models.fit_power_law(alpha, K, rmax)
+    r = np.arange(1, rmax + 1)
+    V = (x[None, :] * lam[None, :] ** r[:, None]).sum(1)
+    Vo = models.couplings(xo, lo, rmax)
+    f = r ** -alpha
+    err_lib = np.abs(V - f).max()
+    err_or = np.abs(Vo - f).max()
+    # same method: the two fits agree far below the fit error itself
+    assert err_lib <= 2 * err_or + 1e-12
+    assert np.abs(V - Vo).max() <= max(1e-9, 0.5 * err_or)
+    assert np.allclose(np.sort(lam.real), np.sort(lo.real), rtol=1e-6, atol=1e-9)
+
+
+def test_fit_rejects_bad_arguments(tdvp):
+    with pytest.raises(tdvp.TdvpError):
+        tdvp.fit_power_law(-1.0, 4, 10)
+    with pytest.raises(tdvp.TdvpError):
+        tdvp.fit_power_law(2.0, 0, 10)
+
+
+@pytest.mark.parametrize("seg", [[9], [5, 5], [3, 4, 5], [2, 3, 3, 4], [2, 2, 2, 2, 2, 2],
+                                 [15, 12, 12, 12, 12, 12, 12, 14], [13, 13, 13, 12],
+                                 [65, 12] + [4] * 12 + [12, 64]])
+@pytest.mark.parametrize("merge", [0, 1])
+def test_schedule_matches_oracle(tdvp, seg, merge):
+    N = sum(seg)
+    for half in (1, 2):
+        lib_ops = tdvp.schedule(N, seg, merge, half)
+        ora = T.build_half(N, seg, half, merge)
+        ref = np.array([[o.seg, 0 if o.kind == "fwd2" else 1, o.j, o.tfac,
+                         (1 if "L" in o.env else 0) | (2 if "R" in o.env else 0),
+                         int(o.boundary), o.stage] for o in ora], dtype=np.int32)
+        assert lib_ops.shape == ref.shape
+        assert np.array_equal(lib_ops, ref)
+
+
+def test_schedule_rejects_short_segment(tdvp):
+    with pytest.raises(tdvp.TdvpError):
+        tdvp.schedule(5, [1, 4], 1, 1)
+    with pytest.raises(tdvp.TdvpError):
+        tdvp.schedule(6, [3, 4], 1, 1)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 8, 16, 24])
+@pytest.mark.parametrize("t", [0.01, -0.3, 2.0])
+def test_tridiag_expm_matches_scipy(tdvp, k, t):
+    rng = np.random.default_rng(k)
+    a = rng.standard_normal(k) * 3
+    b = np.abs(rng.standard_normal(k - 1)) + 0.1
+    c = tdvp.tridiag_expm(a, b, t)
+    Tm = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+    ref = scipy.linalg.expm(-1j * t * Tm)[:, 0]
+    assert np.abs(c - ref).max() < 1e-12
+    # and the oracle's (LAPACK) route gives the same vector
+    assert np.abs(c - T.tridiag_expm_e0(a, b, t)).max() < 1e-12
+
+
+def test_tridiag_expm_degenerate_and_zero_offdiagonal(tdvp):
+    a = np.array([1.0, 1.0, 1.0, -2.0])
+    b = np.array([0.0, 0.5, 0.0])
+    c = tdvp.tridiag_expm(a, b, 0.7)
+    Tm = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+    assert np.abs(c - scipy.linalg.expm(-0.7j * Tm)[:, 0]).max() < 1e-13
