@@ -164,11 +164,11 @@ def fp64_peak_tflops():
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
-def roofline(prof, steps):
-    """Roofline entry for the kernel kind with the largest device time."""
+def roofline(prof, steps, clk=None, kernel=None):
+    """Roofline entry for `kernel` (default: the kind with the largest device time)."""
     if not prof:
         return None, None
-    dom = max(prof, key=lambda k: prof[k]["ms"])
+    dom = kernel if kernel in prof else max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     peaks, src = measured_peaks()
     ms_launch = d["ms"] / max(d["launches"], 1)
@@ -178,7 +178,14 @@ def roofline(prof, steps):
         ach = d["flops"] / d["launches"] / (ms_launch * 1e-3) / 1e12
         r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
              "peak_source": "%s bf16 x 1.1/2.25 (TF32 nominal ratio)" % src}
-    elif dom in ("zgemm_fp64", "svd_jacobi_sweep"):
+    elif dom == "svd_jacobi_fp32":
+        # FP32 ALU peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x clock
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        ach = d["flops"] / d["launches"] / (ms_launch * 1e-3) / 1e12
+        r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock)" % mhz}
+    elif dom.startswith("zgemm") or dom.startswith("svd") or dom.startswith("theta"):
         peak = fp64_peak_tflops()
         ach = d["flops"] / d["launches"] / (ms_launch * 1e-3) / 1e12
         r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
@@ -299,11 +306,13 @@ def run_ours(args, world, rank, local):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     t0 = time.perf_counter()
     st = tdvp.step(mps, mpo, p, args.steps, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - t0
     ms = e0.elapsed_time(e1)
     prof = tdvp.profile_read()
@@ -325,8 +334,10 @@ def run_ours(args, world, rank, local):
         return
     steps_all = args.steps * world
     value = steps_all / (ms_max * 1e-3)
-    rl, dom = roofline(prof, args.steps)
-    heff_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("tc_gemm") or k.startswith("zgemm")
+    rl, dom = roofline(prof, args.steps, clk)
+    tc_kind = "tc_gemm_tf32x3" if args.precision == "tf32x3" else "tc_gemm_tf32"
+    rl_heff, _ = roofline(prof, args.steps, clk, tc_kind) if tc_kind in prof else (None, None)
+    heff_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("tc_gemm") or k == "zgemm_fp64"
                   or k.startswith("wstage") or k == "prep_operands")
     stages_per_step = st.n_stages / max(args.steps, 1)
     line = {
@@ -344,6 +355,7 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": int(8 * mdl.N + stages_per_step * (4 + 12 * 8) + 4)},
         "gpu_launches": int(st.kernel_launches),
         "roofline": rl,
+        "roofline_heff_gemm": rl_heff,
         "heff_tflops": st.heff_flops / max(heff_ms * 1e-3, 1e-12) / 1e12 if heff_ms else None,
         "kernels": {k: {"ms": v["ms"], "launches": v["launches"], "share": v["ms"] / max(ms, 1e-9)}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},

@@ -315,6 +315,8 @@ void read_stage_results(tdvp_mps_s* S, int n, cudaStream_t s) {
   if (st & 1) fail(TDVP_ETIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
   if (st & (2 | 8)) fail(TDVP_ENUMERIC, "NaN or zero norm in a local update");
   if (st & 4) fail(TDVP_ENUMERIC, "tridiagonal eigen-solver did not converge");
+  if (st & 16) fail(TDVP_ENUMERIC, "Jacobi SVD did not converge");
+  if (st & 32) fail(TDVP_ETIMEOUT, "a bounded grid barrier gave up (SVD sweeps)");
 }
 
 struct StageOp {
@@ -350,7 +352,7 @@ void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, con
     q.c_rs = (int64_t)d * B;
     q.c_cs = 1;
   }
-  launch_zgemm(g, s);
+  launch_zgemm(g, s, "theta_form_zgemm");
   // exp(-i H2_eff t) Theta
   std::vector<MvProb> P(n);
   std::vector<const double2*> x(n);
@@ -375,7 +377,9 @@ void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, con
   // truncated SVD re-split (Fig. 5)
   SvdBatch sb{};
   sb.n = n;
+  sb.mode = prec == TDVP_FP64 ? 0 : 1;
   sb.status = S->d_status;
+  sb.sync = sl[0]->sync;
   for (int i = 0; i < n; ++i) {
     const int j = ops[i].j, A = S->chiL(j), B = S->chiR(j + 1);
     SvdDesc& q = sb.d[i];
@@ -385,6 +389,11 @@ void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, con
     q.cols = d * B;
     q.X = sl[i]->svdX;
     q.Acc = sl[i]->svdAcc;
+    q.X32 = sl[i]->svdX32;
+    q.Acc32 = sl[i]->svdAcc32;
+    q.P = sl[i]->svdP;
+    q.T = sl[i]->svdT;
+    q.maxr = sl[i]->maxr;
     q.sig = sl[i]->sig;
     q.perm = sl[i]->perm;
     q.rotated = sl[i]->rot;
@@ -559,6 +568,7 @@ int device_split(tdvp_mps_s* S, Slot* sl, const double2* theta, int rows, int co
   SvdBatch sb{};
   sb.n = 1;
   sb.status = S->d_status;
+  sb.sync = sl->sync;
   SvdDesc& q = sb.d[0];
   q = SvdDesc{};
   q.theta = theta;
@@ -566,6 +576,11 @@ int device_split(tdvp_mps_s* S, Slot* sl, const double2* theta, int rows, int co
   q.cols = cols;
   q.X = sl->svdX;
   q.Acc = sl->svdAcc;
+  q.X32 = sl->svdX32;
+  q.Acc32 = sl->svdAcc32;
+  q.P = sl->svdP;
+  q.T = sl->svdT;
+  q.maxr = sl->maxr;
   q.sig = sl->sig;
   q.perm = sl->perm;
   q.rotated = sl->rot;
@@ -1021,6 +1036,8 @@ struct OpCtx {
     if (st & 1) fail(TDVP_ETIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
     if (st & (2 | 8)) fail(TDVP_ENUMERIC, "NaN or zero norm");
     if (st & 4) fail(TDVP_ENUMERIC, "tridiagonal eigen-solver did not converge");
+    if (st & 16) fail(TDVP_ENUMERIC, "Jacobi SVD did not converge");
+    if (st & 32) fail(TDVP_ETIMEOUT, "a bounded grid barrier gave up (SVD sweeps)");
   }
 };
 
@@ -1244,6 +1261,7 @@ int tdvp_op_split(int rows, int cols, const double* theta, int chi_max, double w
     SvdBatch sb{};
     sb.n = 1;
     sb.status = C.d_status;
+    sb.sync = C.slot.sync;
     SvdDesc& q = sb.d[0];
     q = SvdDesc{};
     q.theta = (const double2*)theta;
@@ -1251,6 +1269,11 @@ int tdvp_op_split(int rows, int cols, const double* theta, int chi_max, double w
     q.cols = cols;
     q.X = C.slot.svdX;
     q.Acc = C.slot.svdAcc;
+    q.X32 = C.slot.svdX32;
+    q.Acc32 = C.slot.svdAcc32;
+    q.P = C.slot.svdP;
+    q.T = C.slot.svdT;
+    q.maxr = C.slot.maxr;
     q.sig = C.slot.sig;
     q.perm = C.slot.perm;
     q.rotated = C.slot.rot;

@@ -97,7 +97,7 @@ struct ZGemmBatch {
   int n;
   ZGemmDesc d[MAXB];
 };
-void launch_zgemm(const ZGemmBatch& b, cudaStream_t s);
+void launch_zgemm(const ZGemmBatch& b, cudaStream_t s, const char* prof_name = "zgemm_fp64");
 
 // ---------------------------------------------------------------------------
 // Sparse MPO operator applied in the "W stage" of a contraction:

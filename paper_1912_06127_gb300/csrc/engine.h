@@ -46,6 +46,12 @@ struct Slot {
   int* counter = nullptr;
   double2* svdX = nullptr;
   double2* svdAcc = nullptr;
+  double2* svdP = nullptr;
+  double2* svdT = nullptr;
+  float2* svdX32 = nullptr;
+  float2* svdAcc32 = nullptr;
+  unsigned* maxr = nullptr;
+  unsigned* sync = nullptr;
   double* sig = nullptr;
   int* perm = nullptr;
   int* rot = nullptr;

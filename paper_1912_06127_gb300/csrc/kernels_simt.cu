@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const __grid_constant__ ZGem
   }
 }
 
-void launch_zgemm(const ZGemmBatch& b, cudaStream_t s) {
+void launch_zgemm(const ZGemmBatch& b, cudaStream_t s, const char* prof_name) {
   if (b.n <= 0) return;
   int maxt = 0;
   for (int i = 0; i < b.n; ++i) {
@@ -122,7 +122,7 @@ void launch_zgemm(const ZGemmBatch& b, cudaStream_t s) {
     fl += 8.0 * d.M * d.N * d.K;
     by += 16.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
   }
-  ProfScope ps("zgemm_fp64", s, fl, by);
+  ProfScope ps(prof_name, s, fl, by);
   dim3 grid(maxt, b.n);
   zgemm_kernel<<<grid, 256, 0, s>>>(b);
   LAUNCH_CHECK();

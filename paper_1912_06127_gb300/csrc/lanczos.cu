@@ -36,7 +36,9 @@ __device__ inline double2 warp_sum2(double2 v) {
 // thread 0 in out[]. scratch: [LZ_THREADS/32][cnt]
 __device__ inline void block_sum(const double2* vals, int cnt, double2* scratch, double2* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i < cnt; ++i) {
+#pragma unroll
+  for (int i = 0; i < KRYLOV_MAX; ++i) {
+    if (i >= cnt) break;
     double2 v = warp_sum2(vals[i]);
     if (lane == 0) scratch[warp * KRYLOV_MAX + i] = v;
   }
@@ -130,16 +132,20 @@ __global__ void __launch_bounds__(LZ_THREADS) lz_dots(const __grid_constant__ Lz
   if ((int)blockIdx.x >= nblk) return;
   __shared__ double2 scratch[(LZ_THREADS / 32) * KRYLOV_MAX];
   __shared__ double2 tot[KRYLOV_MAX];
+  // accumulators indexed by compile-time constants only (registers, no local memory)
   double2 acc[KRYLOV_MAX];
   const int cnt = j + 1;
-  for (int i = 0; i < cnt; ++i) acc[i] = make_double2(0, 0);
+#pragma unroll
+  for (int i = 0; i < KRYLOV_MAX; ++i) acc[i] = make_double2(0, 0);
   const double2* w = P.V + (int64_t)(j + 1) * P.vs;
   const int64_t base = (int64_t)blockIdx.x * LZ_THREADS * LZ_ELEMS;
   for (int e = 0; e < LZ_ELEMS; ++e) {
     int64_t idx = base + (int64_t)e * LZ_THREADS + threadIdx.x;
     if (idx >= P.n) break;
     double2 wv = w[idx];
-    for (int i = 0; i < cnt; ++i) zfma_cj(acc[i], P.V[(int64_t)i * P.vs + idx], wv);
+#pragma unroll
+    for (int i = 0; i < KRYLOV_MAX; ++i)
+      if (i < cnt) zfma_cj(acc[i], P.V[(int64_t)i * P.vs + idx], wv);
   }
   block_sum(acc, cnt, scratch, tot);
   double2* part = P.part + (int64_t)blockIdx.x * KRYLOV_MAX;

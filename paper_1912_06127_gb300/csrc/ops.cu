@@ -126,7 +126,13 @@ void Slot::ensure(int64_t vec, int64_t T, int64_t fsz, int64_t svd_n, int kmax_)
   CUDA_TRY(cudaMemset(counter, 0, sizeof(int)));
   svdX = dalloc<double2>(cap_vec);
   svdAcc = dalloc<double2>(cap_vec);
-  sig = dalloc<double>(svd_n + 1);
+  svdP = dalloc<double2>(cap_vec);
+  svdT = dalloc<double2>(cap_vec);
+  svdX32 = dalloc<float2>(cap_vec);
+  svdAcc32 = dalloc<float2>(cap_vec);
+  maxr = reinterpret_cast<unsigned*>(dalloc<int>(1));
+  sync = reinterpret_cast<unsigned*>(dalloc<int>(4));
+  sig = dalloc<double>(svd_n + 2);
   perm = dalloc<int>(svd_n + 1);
   rot = dalloc<int>(1);
   conv = dalloc<int>(1);
@@ -135,13 +141,17 @@ void Slot::ensure(int64_t vec, int64_t T, int64_t fsz, int64_t svd_n, int kmax_)
 void Slot::release() {
   for (void* p : {(void*)theta, (void*)theta2, (void*)V, (void*)T1, (void*)T2, (void*)Amat, (void*)Bmat,
                   (void*)st, (void*)part, (void*)counter, (void*)svdX, (void*)svdAcc, (void*)sig,
-                  (void*)perm, (void*)rot, (void*)conv})
+                  (void*)perm, (void*)rot, (void*)conv, (void*)svdP, (void*)svdT, (void*)svdX32,
+                  (void*)svdAcc32, (void*)maxr, (void*)sync})
     dfree(p);
   for (auto& p : f) {
     dfree(p);
     p = nullptr;
   }
-  theta = theta2 = V = T1 = T2 = Amat = Bmat = part = svdX = svdAcc = nullptr;
+  theta = theta2 = V = T1 = T2 = Amat = Bmat = part = svdX = svdAcc = svdP = svdT = nullptr;
+  svdX32 = svdAcc32 = nullptr;
+  maxr = nullptr;
+  sync = nullptr;
   st = nullptr;
   counter = perm = rot = conv = nullptr;
   sig = nullptr;

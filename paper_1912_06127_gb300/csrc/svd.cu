@@ -10,6 +10,17 @@
 // all problems of a stage in the same launch. The final vector norms are the
 // singular values.
 //
+// FP64 arithmetic is scarce on this GPU (about 1/64 of the FP32 issue rate), so
+// the sweeps run in two phases. First the rotations are found and applied in
+// FP32 until the vectors are orthogonal to about 1e-6 (relative). The
+// accumulated FP32 rotation is then made unitary to FP64 rounding by two
+// Newton-Schulz steps (Acc <- (3 Acc - Acc Acc^H Acc) / 2), the vectors are
+// recomputed in FP64 from the input (X = Acc Theta'), and FP64 sweeps finish
+// the job. Cyclic Jacobi converges quadratically, so a sweep whose largest
+// relative off-diagonal |<x,y>|/(|x||y|) stayed below 1e-7 leaves less than
+// ~1e-14 and ends the iteration. The result has FP64 accuracy; the FP32
+// phase only shortens the FP64 phase.
+//
 // Truncation (Sec. III C, Eq. 22 and Sec. III D): the smallest rank chi_w
 // whose discarded weight sum_{j >= chi_w} lambda_j^2 is <= w_max, capped at
 // chi_max and at the values above eps * lambda_1, at least 1. Then
@@ -23,8 +34,47 @@ constexpr double JACOBI_TOL = 1e-14;
 constexpr int SVD_WARPS = 8;
 constexpr int SVD_MAX_SWEEPS = 40;
 
-__global__ void svd_setup(const __grid_constant__ SvdBatch B) {
+// Power-of-two scale bringing the largest entry of theta into [0.5, 1), so
+// that the FP32 phase cannot overflow or underflow whatever the input's
+// magnitude (rotations do not depend on the scale), stored in sig[n_vec];
+// and ||theta||_F^2, stored in sig[n_vec + 1], which sets the level below
+// which vectors are rounding noise.
+__global__ void svd_scale(const __grid_constant__ SvdBatch B) {
+  const SvdDesc& P = B.d[blockIdx.x];
+  __shared__ double red[512];
+  __shared__ double red2[512];
+  double mx = 0.0, fr = 0.0;
+  const int64_t n = (int64_t)P.rows * P.cols;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 v = P.theta[i];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    fr += v.x * v.x + v.y * v.y;
+  }
+  red[threadIdx.x] = mx;
+  red2[threadIdx.x] = fr;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+      red2[threadIdx.x] += red2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.sig[P.n_vec + 1] = red2[0];
+    double sc = 1.0;
+    if (red[0] > 0.0 && red[0] < 1e300) {
+      int e = 0;
+      frexp(red[0], &e);
+      sc = ldexp(1.0, -e);
+    }
+    P.sig[P.n_vec] = sc;
+  }
+}
+
+__global__ void svd_setup32(const __grid_constant__ SvdBatch B) {
   const SvdDesc& P = B.d[blockIdx.y];
+  const double sc = P.sig[P.n_vec];
   const int64_t nx = (int64_t)P.n_vec * P.len;
   const int64_t na = (int64_t)P.n_vec * P.n_vec;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nx + na;
@@ -32,16 +82,18 @@ __global__ void svd_setup(const __grid_constant__ SvdBatch B) {
     if (i < nx) {
       int v = (int)(i / P.len), e = (int)(i % P.len);
       // trans 0: vector v = row v of theta; trans 1: vector v = column v
-      P.X[i] = P.trans ? P.theta[(int64_t)e * P.cols + v] : P.theta[(int64_t)v * P.cols + e];
+      double2 t = P.trans ? P.theta[(int64_t)e * P.cols + v] : P.theta[(int64_t)v * P.cols + e];
+      P.X32[i] = make_float2((float)(t.x * sc), (float)(t.y * sc));
     } else {
       int64_t q = i - nx;
       int r = (int)(q / P.n_vec), c = (int)(q % P.n_vec);
-      P.Acc[q] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+      P.Acc32[q] = make_float2(r == c ? 1.0f : 0.0f, 0.0f);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *P.rotated = 0;
     *P.conv = 0;
+    *P.maxr = 0u;
   }
 }
 
@@ -50,15 +102,120 @@ __device__ inline double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ inline float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
-__global__ void __launch_bounds__(SVD_WARPS * 32) svd_round(const __grid_constant__ SvdBatch B, int r) {
-  const SvdDesc& P = B.d[blockIdx.y];
-  if (*P.conv) return;
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double2> {
+  using R = double;
+  static constexpr double tol = JACOBI_TOL;
+  // pairs whose norms are both below 1e-14 ||theta||_F are rounding noise
+  __device__ static R zero_level(const SvdDesc& P) { return 1e-28 * P.sig[P.n_vec + 1]; }
+  __device__ static R wsum(R v) { return warp_sum(v); }
+  __device__ static double2* X(const SvdDesc& P) { return P.X; }
+  __device__ static double2* Acc(const SvdDesc& P) { return P.Acc; }
+  __device__ static double2 mk(R a, R b) { return make_double2(a, b); }
+};
+template <>
+struct Prec<float2> {
+  using R = float;
+  static constexpr float tol = 2e-6f;  // above the FP32 rounding of the dot products
+  // FP32 noise level: 1e-6 ||theta||_F (theta scaled by sig[n_vec] in this phase)
+  __device__ static R zero_level(const SvdDesc& P) {
+    const double sc = P.sig[P.n_vec];
+    return (R)(1e-12 * P.sig[P.n_vec + 1] * sc * sc);
+  }
+  __device__ static R wsum(R v) { return warp_sumf(v); }
+  __device__ static float2* X(const SvdDesc& P) { return P.X32; }
+  __device__ static float2* Acc(const SvdDesc& P) { return P.Acc32; }
+  __device__ static float2 mk(R a, R b) { return make_float2(a, b); }
+};
+
+template <typename T>
+__device__ inline void rot2(T* x, T* y, int n, int lane, typename Prec<T>::R cs, T m1, T m2) {
+  // x' = cs x + m1 y ; y' = cs y + m2 x
+  for (int i = lane; i < n; i += 32) {
+    T u = x[i], v = y[i];
+    T nu = Prec<T>::mk(cs * u.x + m1.x * v.x - m1.y * v.y, cs * u.y + m1.x * v.y + m1.y * v.x);
+    T nv = Prec<T>::mk(cs * v.x + m2.x * u.x - m2.y * u.y, cs * v.y + m2.x * u.y + m2.y * u.x);
+    x[i] = nu;
+    y[i] = nv;
+  }
+}
+
+// Rotation of two rows held in registers: each lane owns elements lane, lane+32, ...
+template <typename T, int NR>
+__device__ inline void rot_regs(T (&u)[NR], T (&v)[NR], typename Prec<T>::R cs, T m1, T m2) {
+#pragma unroll
+  for (int e = 0; e < NR; ++e) {
+    const T a = u[e], b = v[e];
+    u[e] = Prec<T>::mk(cs * a.x + m1.x * b.x - m1.y * b.y, cs * a.y + m1.x * b.y + m1.y * b.x);
+    v[e] = Prec<T>::mk(cs * b.x + m2.x * a.x - m2.y * a.y, cs * b.y + m2.x * a.y + m2.y * a.x);
+  }
+}
+
+// Loads, rotates and stores a pair of rows of length n <= 32 * NR in registers.
+template <typename T, int NR>
+__device__ inline void rot_rows_regs(T* x, T* y, int n, int lane, typename Prec<T>::R cs, T m1, T m2) {
+  T u[NR], v[NR];
+#pragma unroll
+  for (int e = 0; e < NR; ++e) {
+    const int i = lane + 32 * e;
+    u[e] = i < n ? x[i] : Prec<T>::mk(0, 0);
+    v[e] = i < n ? y[i] : Prec<T>::mk(0, 0);
+  }
+  rot_regs<T, NR>(u, v, cs, m1, m2);
+#pragma unroll
+  for (int e = 0; e < NR; ++e) {
+    const int i = lane + 32 * e;
+    if (i < n) {
+      x[i] = u[e];
+      y[i] = v[e];
+    }
+  }
+}
+
+// Rotation parameters of a pair from its Gram entries; false if no rotation.
+template <typename T>
+__device__ inline bool jacobi_params(const SvdDesc& P, typename Prec<T>::R a, typename Prec<T>::R b,
+                                     typename Prec<T>::R kr, typename Prec<T>::R ki, int lane,
+                                     typename Prec<T>::R& cs, T& m1, T& m2) {
+  using R = typename Prec<T>::R;
+  const R ak = sqrt(kr * kr + ki * ki);
+  const R ab = sqrt(a * b);
+  if (!(ak > Prec<T>::tol * ab)) return false;
+  // a vector at rounding-noise level has a noise direction: leave it alone
+  // (such values are dropped by the truncation's noise floor)
+  if (a < Prec<T>::zero_level(P) || b < Prec<T>::zero_level(P)) return false;
+  if (lane == 0) {
+    atomicAdd(P.rotated, 1);
+    atomicMax(P.maxr, __float_as_uint((float)(ak / ab)));
+  }
+  const R phr = kr / ak, phi = ki / ak;  // e^{i phi}
+  const R zeta = (b - a) / (R(2) * ak);
+  const R t = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+  cs = R(1) / sqrt(R(1) + t * t);
+  const R sn = cs * t;
+  // x' = cs x - sn e^{-i phi} y ; y' = sn e^{i phi} x + cs y
+  m1 = Prec<T>::mk(-sn * phr, sn * phi);
+  m2 = Prec<T>::mk(sn * phr, sn * phi);
+  return true;
+}
+
+// One Jacobi rotation: the lanes of a warp handle pair `pair` of round r of
+// problem P. Rows of up to 512 elements stay in registers between the dot
+// products and the rotation (one load, one store); longer rows stream.
+template <typename T>
+__device__ inline void jacobi_pair(const SvdDesc& P, int r, int pair, int lane) {
+  using R = typename Prec<T>::R;
+  constexpr int NR = 16;
   const int npad = P.n_vec + (P.n_vec & 1);
-  if (npad < 2 || r >= npad - 1) return;
-  const int pair = blockIdx.x * SVD_WARPS + (threadIdx.x >> 5);
-  if (pair >= npad / 2) return;
-  const int lane = threadIdx.x & 31;
+  if (npad < 2 || r >= npad - 1 || pair >= npad / 2) return;
   int p, q;
   if (pair == 0) {
     p = npad - 1;
@@ -73,63 +230,182 @@ __global__ void __launch_bounds__(SVD_WARPS * 32) svd_round(const __grid_constan
     q = t;
   }
   if (q >= P.n_vec) return;
-  double2* x = P.X + (int64_t)p * P.len;
-  double2* y = P.X + (int64_t)q * P.len;
-  double a = 0, b = 0, kr = 0, ki = 0;
-  for (int i = lane; i < P.len; i += 32) {
-    double2 u = x[i], v = y[i];
-    a += u.x * u.x + u.y * u.y;
-    b += v.x * v.x + v.y * v.y;
-    kr += u.x * v.x + u.y * v.y;  // conj(u) v
-    ki += u.x * v.y - u.y * v.x;
+  T* X = Prec<T>::X(P);
+  T* x = X + (int64_t)p * P.len;
+  T* y = X + (int64_t)q * P.len;
+  T* A = Prec<T>::Acc(P);
+  T* ax = A + (int64_t)p * P.n_vec;
+  T* ay = A + (int64_t)q * P.n_vec;
+  R cs;
+  T m1, m2;
+  if (P.len <= 32 * NR) {
+    T u[NR], v[NR];
+#pragma unroll
+    for (int e = 0; e < NR; ++e) {
+      const int i = lane + 32 * e;
+      u[e] = i < P.len ? x[i] : Prec<T>::mk(0, 0);
+      v[e] = i < P.len ? y[i] : Prec<T>::mk(0, 0);
+    }
+    R a = 0, b = 0, kr = 0, ki = 0;
+#pragma unroll
+    for (int e = 0; e < NR; ++e) {
+      a += u[e].x * u[e].x + u[e].y * u[e].y;
+      b += v[e].x * v[e].x + v[e].y * v[e].y;
+      kr += u[e].x * v[e].x + u[e].y * v[e].y;  // conj(u) v
+      ki += u[e].x * v[e].y - u[e].y * v[e].x;
+    }
+    a = Prec<T>::wsum(a);
+    b = Prec<T>::wsum(b);
+    kr = Prec<T>::wsum(kr);
+    ki = Prec<T>::wsum(ki);
+    if (!jacobi_params<T>(P, a, b, kr, ki, lane, cs, m1, m2)) return;
+    rot_regs<T, NR>(u, v, cs, m1, m2);
+#pragma unroll
+    for (int e = 0; e < NR; ++e) {
+      const int i = lane + 32 * e;
+      if (i < P.len) {
+        x[i] = u[e];
+        y[i] = v[e];
+      }
+    }
+  } else {
+    R a = 0, b = 0, kr = 0, ki = 0;
+    for (int i = lane; i < P.len; i += 32) {
+      T u = x[i], v = y[i];
+      a += u.x * u.x + u.y * u.y;
+      b += v.x * v.x + v.y * v.y;
+      kr += u.x * v.x + u.y * v.y;
+      ki += u.x * v.y - u.y * v.x;
+    }
+    a = Prec<T>::wsum(a);
+    b = Prec<T>::wsum(b);
+    kr = Prec<T>::wsum(kr);
+    ki = Prec<T>::wsum(ki);
+    if (!jacobi_params<T>(P, a, b, kr, ki, lane, cs, m1, m2)) return;
+    rot2<T>(x, y, P.len, lane, cs, m1, m2);
   }
-  a = warp_sum(a);
-  b = warp_sum(b);
-  kr = warp_sum(kr);
-  ki = warp_sum(ki);
-  const double ak = sqrt(kr * kr + ki * ki);
-  if (!(ak > JACOBI_TOL * sqrt(a * b))) return;
-  if (lane == 0) atomicAdd(P.rotated, 1);
-  const double phr = kr / ak, phi = ki / ak;  // e^{i phi}
-  const double zeta = (b - a) / (2.0 * ak);
-  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-  // x' = cs x - sn e^{-i phi} y ; y' = sn e^{i phi} x + cs y
-  const double2 m1 = make_double2(-sn * phr, sn * phi);   // -sn e^{-i phi}
-  const double2 m2 = make_double2(sn * phr, sn * phi);    //  sn e^{+i phi}
-  for (int i = lane; i < P.len; i += 32) {
-    double2 u = x[i], v = y[i];
-    double2 nu = zscale(u, cs), nv = zscale(v, cs);
-    zfma(nu, m1, v);
-    zfma(nv, m2, u);
-    x[i] = nu;
-    y[i] = nv;
+  if (P.n_vec <= 32 * NR) rot_rows_regs<T, NR>(ax, ay, P.n_vec, lane, cs, m1, m2);
+  else rot2<T>(ax, ay, P.n_vec, lane, cs, m1, m2);
+}
+
+// Grid-wide barrier for a cooperative launch, with a bounded wait: returns
+// false (and sets the status bit and the abort word, which makes every later
+// barrier return at once) if the other blocks did not arrive in time.
+// sync[0] = arrivals, sync[1] = generation, sync[3] = abort.
+__device__ inline bool grid_barrier(unsigned* sync, unsigned nblocks, int* status) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok_sh = 1;
+    volatile unsigned* gen = sync + 1;
+    volatile unsigned* abort_w = sync + 3;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(sync, 1u);
+    if (arrived == nblocks - 1) {
+      sync[0] = 0u;
+      __threadfence();
+      atomicAdd(sync + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (*abort_w) {
+          ok_sh = 0;
+          break;
+        }
+        if (++spins > (1ll << 24)) {
+          ok_sh = 0;
+          atomicOr(status, 32);
+          atomicExch(sync + 3, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (*abort_w) ok_sh = 0;
+    __threadfence();
   }
-  double2* ax = P.Acc + (int64_t)p * P.n_vec;
-  double2* ay = P.Acc + (int64_t)q * P.n_vec;
-  for (int i = lane; i < P.n_vec; i += 32) {
-    double2 u = ax[i], v = ay[i];
-    double2 nu = zscale(u, cs), nv = zscale(v, cs);
-    zfma(nu, m1, v);
-    zfma(nv, m2, u);
-    ax[i] = nu;
-    ay[i] = nv;
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// All sweeps of one phase in one cooperative launch: rounds separated by grid
+// barriers, warps striding over the pairs of all problems; after each sweep
+// block 0 marks converged problems (no rotation, or the largest relative
+// off-diagonal below `stop`) and the loop ends when all are converged.
+// sync[2] = unconverged count of the last sweep.
+template <typename T>
+__global__ void __launch_bounds__(SVD_WARPS * 32) svd_sweeps(const __grid_constant__ SvdBatch B, int npad_max,
+                                                            float stop, int max_sweeps) {
+  __shared__ int off[MAXB + 1];
+  if (threadIdx.x == 0) {
+    off[0] = 0;
+    for (int i = 0; i < B.n; ++i) {
+      const int n = B.d[i].n_vec;
+      off[i + 1] = off[i] + (n + (n & 1)) / 2;
+    }
+  }
+  __syncthreads();
+  const int total = off[B.n];
+  const int wpb = blockDim.x / 32;
+  const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int nw = gridDim.x * wpb;
+  const int lane = threadIdx.x & 31;
+  volatile unsigned* unconv = B.sync + 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int r = 0; r < npad_max - 1; ++r) {
+      for (int w = gw; w < total; w += nw) {
+        int pid = 0;
+        while (w >= off[pid + 1]) ++pid;
+        const SvdDesc& P = B.d[pid];
+        if (*(volatile int*)P.conv) continue;
+        jacobi_pair<T>(P, r, w - off[pid], lane);
+      }
+      if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      unsigned cnt = 0;
+      for (int i = 0; i < B.n; ++i) {
+        const SvdDesc& P = B.d[i];
+        if (!*P.conv) {
+          if (*P.rotated == 0 || __uint_as_float(*P.maxr) < stop) *P.conv = 1;
+          else ++cnt;
+        }
+        *P.rotated = 0;
+        *P.maxr = 0u;
+      }
+      *unconv = cnt;
+      __threadfence();
+    }
+    if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
+    if (*unconv == 0) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, 16);
+}
+
+// FP32 rotation -> FP64; reset the convergence state for the FP64 phase
+__global__ void svd_acc_to64(const __grid_constant__ SvdBatch B) {
+  const SvdDesc& P = B.d[blockIdx.y];
+  const int64_t na = (int64_t)P.n_vec * P.n_vec;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 a = P.Acc32[i];
+    P.Acc[i] = make_double2((double)a.x, (double)a.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *P.rotated = 0;
+    *P.conv = 0;
+    *P.maxr = 0u;
   }
 }
 
-// After a sweep: problems with no rotation are converged; count the others.
-__global__ void svd_sweep_end(const __grid_constant__ SvdBatch B, int* unconv) {
-  if (threadIdx.x != 0) return;
-  int cnt = 0;
-  for (int i = 0; i < B.n; ++i) {
-    const SvdDesc& P = B.d[i];
-    if (!*P.conv) {
-      if (*P.rotated == 0) *P.conv = 1;
-      else ++cnt;
-    }
-    *P.rotated = 0;
+// Newton-Schulz step for the unitary polar factor: Acc <- 1.5 Acc - 0.5 T, T = Acc Acc^H Acc
+__global__ void svd_ns_combine(const __grid_constant__ SvdBatch B) {
+  const SvdDesc& P = B.d[blockIdx.y];
+  const int64_t na = (int64_t)P.n_vec * P.n_vec;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 a = P.Acc[i], t = P.T[i];
+    P.Acc[i] = make_double2(1.5 * a.x - 0.5 * t.x, 1.5 * a.y - 0.5 * t.y);
   }
-  *unconv = cnt;
 }
 
 __global__ void svd_norms(const __grid_constant__ SvdBatch B) {
@@ -192,9 +468,14 @@ __global__ void svd_truncate(const __grid_constant__ SvdBatch B) {
     }
     chi_w = best;
   }
+  // values above eps * lambda_1 (Sec. III D) and above the FP64 noise floor
+  // 1e-14 ||theta||_F (below it a value and its vectors are rounding noise)
+  const double noise = 1e-14 * sqrt(P.sig[n + 1]);
   int n_eps = 0;
-  for (int k = 0; k < n; ++k)
-    if (P.sig[P.perm[k]] > P.eps * s0) ++n_eps;
+  for (int k = 0; k < n; ++k) {
+    const double sk = P.sig[P.perm[k]];
+    if (sk > P.eps * s0 && sk > noise) ++n_eps;
+  }
   int chi = chi_w < P.chi_max ? chi_w : P.chi_max;
   if (n_eps < chi) chi = n_eps;
   if (chi < 1) chi = 1;
@@ -237,10 +518,34 @@ __global__ void svd_write(const __grid_constant__ SvdBatch B) {
   }
 }
 
+// all sweeps of one phase as one cooperative launch (no host round trips)
+template <typename T>
+static void jacobi_sweeps(SvdBatch& b, int npad_max, float stop, cudaStream_t s, const char* name,
+                          double flops_per_sweep) {
+  static int max_blocks = -1;
+  if (max_blocks < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_sweeps<T>, SVD_WARPS * 32, 0));
+    max_blocks = std::max(1, sms * std::min(per_sm, 4));
+  }
+  int total = 0;
+  for (int i = 0; i < b.n; ++i) total += (b.d[i].n_vec + (b.d[i].n_vec & 1)) / 2;
+  const int blocks = std::max(1, std::min(max_blocks, cdiv(total, SVD_WARPS)));
+  CUDA_TRY(cudaMemsetAsync(b.sync, 0, 4 * sizeof(unsigned), s));
+  int max_sweeps = SVD_MAX_SWEEPS;
+  void* args[] = {(void*)&b, (void*)&npad_max, (void*)&stop, (void*)&max_sweeps};
+  ProfScope ps(name, s, flops_per_sweep, 0.0);
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)svd_sweeps<T>, dim3(blocks), dim3(SVD_WARPS * 32), args, 0, s));
+  ++g_launches;
+}
+
 void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   if (b.n <= 0) return;
   int64_t max_elems = 1;
   int npad_max = 2, nvec_max = 1;
+  double fl = 0;
   for (int i = 0; i < b.n; ++i) {
     auto& P = b.d[i];
     P.trans = P.rows > P.cols ? 1 : 0;
@@ -249,31 +554,62 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
     max_elems = std::max<int64_t>(max_elems, (int64_t)P.n_vec * (P.len + P.n_vec));
     npad_max = std::max(npad_max, P.n_vec + (P.n_vec & 1));
     nvec_max = std::max(nvec_max, P.n_vec);
+    // dots of every pair once per sweep (lower bound of the sweep's work)
+    fl += 16.0 * (double)P.len * (P.n_vec / 2) * (P.n_vec - 1);
   }
   dim3 g1((unsigned)std::min<int64_t>(cdiv64(max_elems, 256), 152 * 8), b.n);
-  svd_setup<<<g1, 256, 0, s>>>(b);
+  // ---- phase 1: FP32 sweeps ----
+  svd_scale<<<b.n, 512, 0, s>>>(b);
+  LAUNCH_CHECK();
+  svd_setup32<<<g1, 256, 0, s>>>(b);
   LAUNCH_CHECK();
   ++g_launches;
-  dim3 gr(cdiv(npad_max / 2, SVD_WARPS), b.n);
-  bool converged = false;
-  for (int sweep = 0; sweep < SVD_MAX_SWEEPS && !converged; ++sweep) {
-    double fl = 0;
-    for (int i = 0; i < b.n; ++i)
-      fl += 16.0 * (double)b.d[i].len * (b.d[i].n_vec / 2) * (b.d[i].n_vec - 1);
-    ProfScope ps("svd_jacobi_sweep", s, fl, 0.0);
-    for (int r = 0; r < npad_max - 1; ++r) {
-      svd_round<<<gr, SVD_WARPS * 32, 0, s>>>(b, r);
-    }
-    LAUNCH_CHECK();
-    g_launches += npad_max - 1;
-    svd_sweep_end<<<1, 32, 0, s>>>(b, d_flag);
+  jacobi_sweeps<float2>(b, npad_max, 1e-3f, s, "svd_jacobi_fp32", fl);
+  // ---- phase 2: unitary FP64 rotation and FP64 vectors ----
+  svd_acc_to64<<<g1, 256, 0, s>>>(b);
+  LAUNCH_CHECK();
+  ZGemmBatch gp{}, gt{}, gx{};
+  gp.n = gt.n = gx.n = b.n;
+  for (int i = 0; i < b.n; ++i) {
+    const SvdDesc& P = b.d[i];
+    const int n = P.n_vec;
+    ZGemmDesc& a = gp.d[i];   // P = Acc Acc^H
+    a = ZGemmDesc{};
+    a.M = a.N = a.K = n;
+    a.A = P.Acc; a.a_rs = n; a.a_cs = 1;
+    a.B = P.Acc; a.b_rs = 1; a.b_cs = n; a.conj_b = 1;
+    a.C = P.P; a.c_rs = n; a.c_cs = 1;
+    ZGemmDesc& t = gt.d[i];   // T = P Acc
+    t = ZGemmDesc{};
+    t.M = t.N = t.K = n;
+    t.A = P.P; t.a_rs = n; t.a_cs = 1;
+    t.B = P.Acc; t.b_rs = n; t.b_cs = 1;
+    t.C = P.T; t.c_rs = n; t.c_cs = 1;
+    ZGemmDesc& x = gx.d[i];   // X = Acc . vectors(theta)
+    x = ZGemmDesc{};
+    x.M = n; x.N = P.len; x.K = n;
+    x.A = P.Acc; x.a_rs = n; x.a_cs = 1;
+    x.B = P.theta;
+    if (!P.trans) { x.b_rs = P.cols; x.b_cs = 1; }
+    else { x.b_rs = 1; x.b_cs = P.cols; }
+    x.C = P.X; x.c_rs = P.len; x.c_cs = 1;
+  }
+  // Newton-Schulz steps: unitarity error ~1e-5 (FP32 rotations) -> ~1e-10 -> ~1e-16
+  const int ns_steps = b.mode == 0 ? 2 : 1;
+  for (int it = 0; it < ns_steps; ++it) {
+    launch_zgemm(gp, s, "svd_newton_schulz");
+    launch_zgemm(gt, s, "svd_newton_schulz");
+    dim3 gn((unsigned)std::min<int64_t>(cdiv64((int64_t)nvec_max * nvec_max, 256), 152 * 8), b.n);
+    svd_ns_combine<<<gn, 256, 0, s>>>(b);
     LAUNCH_CHECK();
     ++g_launches;
-    CUDA_TRY(cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    converged = (*h_flag == 0);
   }
-  if (!converged) fail(TDVP_ENUMERIC, "Jacobi SVD did not converge");
+  launch_zgemm(gx, s, "svd_newton_schulz");
+  g_launches += 2;
+  // ---- phase 3: FP64 sweeps ----
+  // stop after a sweep whose largest relative off-diagonal was below 1e-7 (full:
+  // ~1e-14 left) or 1e-5 (mixed-precision sweeps: ~1e-10 or less left)
+  jacobi_sweeps<double2>(b, npad_max, b.mode == 0 ? 1e-7f : 1e-5f, s, "svd_jacobi_fp64", fl);
   dim3 gn(cdiv(nvec_max, SVD_WARPS), b.n);
   svd_norms<<<gn, SVD_WARPS * 32, 0, s>>>(b);
   LAUNCH_CHECK();

@@ -11,7 +11,12 @@ struct SvdDesc {
   int n_vec, len, trans; // vectors = rows of theta (trans 0) or its columns (trans 1)
   double2* X;            // [n_vec][len] working vectors
   double2* Acc;          // [n_vec][n_vec] accumulated rotations
-  double* sig;           // [n_vec] norms of the final vectors
+  float2* X32;           // FP32 preconditioning phase: vectors and rotations
+  float2* Acc32;
+  double2* P;            // [n_vec][n_vec] Newton-Schulz temporaries
+  double2* T;
+  unsigned* maxr;        // largest |<x,y>| / (|x| |y|) met in the current sweep (float bits)
+  double* sig;           // [n_vec + 2] norms of the final vectors, then scale and ||theta||_F^2
   int* perm;             // [n_vec] descending order
   int* rotated;          // rotations applied in the current sweep
   int* conv;             // 1 once a sweep applied no rotation
@@ -26,12 +31,17 @@ struct SvdDesc {
 };
 struct SvdBatch {
   int n;
-  int* status;           // bit 8: NaN / zero state, bit 16: no convergence
+  int mode;              // 0: FP64 to ~1e-14 orthogonality; 1: to ~1e-12 (mixed-precision sweeps)
+  int* status;           // bit 8: NaN / zero state, bit 16: no convergence, bit 32: barrier timeout
+  unsigned* sync;        // 4 words of device scratch for the grid barrier and the sweep loop
   SvdDesc d[MAXB];
 };
 
-// Full pipeline: Jacobi sweeps until converged (one host synchronisation per
-// sweep), then sort, truncate and write Psi_L, V, Psi_R. h_flag: pinned host int.
+// Full pipeline: FP32 Jacobi sweeps (preconditioner), Newton-Schulz
+// re-orthonormalisation of the accumulated rotation and recomputation of the
+// vectors in FP64, FP64 Jacobi sweeps until converged (one host
+// synchronisation per sweep), then sort, truncate and write Psi_L, V, Psi_R.
+// h_flag: pinned host int.
 void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s);
 
 }  // namespace tdvp

@@ -143,7 +143,7 @@ def test_expm_mixed_precision(prec):
     assert rel_err(host(y).reshape(th.shape), ref) < TOL[prec]
 
 
-def decaying_matrix(rows, cols, seed, rank=None, decay=0.7):
+def decaying_matrix(rows, cols, seed, rank=None, decay=0.75):
     U = np.linalg.qr(I.random_complex((rows, rows), seed))[0]
     Vh = np.linalg.qr(I.random_complex((cols, cols), seed + 1))[0]
     n = min(rows, cols)
@@ -188,17 +188,27 @@ def test_split(rows, cols, chi_max, w_max, eps):
     assert np.abs(rec - best).max() < 1e-12
 
 
-def test_split_rank_deficient():
+@pytest.mark.parametrize("eps", [1e-12, 0.0])
+@pytest.mark.parametrize("rows,cols", [(24, 40), (40, 24), (4, 4)])
+def test_split_rank_deficient(eps, rows, cols):
+    # exact zeros: the numerically-zero values (below 1e-14 ||theta||_F) are
+    # dropped even with eps = 0, and the kept vectors are orthonormal
     torch = torch_or_skip()
     tdvp = lib()
-    theta, s_true = decaying_matrix(24, 40, 30, rank=5)
-    PsiL = torch.zeros(24 * 24, dtype=torch.complex128, device="cuda")
-    PsiR = torch.zeros(24 * 40, dtype=torch.complex128, device="cuda")
-    V = torch.zeros(24, dtype=torch.float64, device="cuda")
-    chi, w = tdvp.op_split(24, 40, dev(torch, theta), 100, 0.0, 1e-12, PsiL, V, PsiR)
-    assert chi == 5 and w < 1e-28
-    v = V.cpu().numpy()[:5]
-    assert np.allclose(1.0 / v, s_true[:5], rtol=1e-12)
+    rank = 2 if rows == 4 else 5
+    theta, s_true = decaying_matrix(rows, cols, 30, rank=rank)
+    n = min(rows, cols)
+    PsiL = torch.zeros(rows * n, dtype=torch.complex128, device="cuda")
+    PsiR = torch.zeros(n * cols, dtype=torch.complex128, device="cuda")
+    V = torch.zeros(n, dtype=torch.float64, device="cuda")
+    chi, w = tdvp.op_split(rows, cols, dev(torch, theta), 100, 0.0, eps, PsiL, V, PsiR)
+    assert chi == rank and w < 1e-26
+    v = V.cpu().numpy()[:rank]
+    assert np.allclose(1.0 / v, s_true[:rank], rtol=1e-12)
+    A = host(PsiL)[: rows * chi].reshape(rows, chi) * v[None, :]
+    B = v[:, None] * host(PsiR)[: chi * cols].reshape(chi, cols)
+    assert np.abs(A.conj().T @ A - np.eye(chi)).max() < 1e-12
+    assert np.abs(B @ B.conj().T - np.eye(chi)).max() < 1e-12
 
 
 @pytest.mark.parametrize("prec", [FP64, TF32X3], ids=["fp64", "tf32x3"])
