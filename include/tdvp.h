@@ -228,6 +228,25 @@ int tdvp_op_split(int rows, int cols, const double* theta, int chi_max, double w
                   double* Psi_L, double* V, double* Psi_R, double* s_out, int* chi, double* w,
                   void* stream);
 
+/* Same as tdvp_op_heff with precision TDVP_FP64, for callers that cannot
+ * allocate device memory (a stream capture that forbids allocation, a host
+ * application that owns every device allocation, a real-time loop). The
+ * paper has no counterpart: this is a deployment variant of the H_eff
+ * application of Fig. 4. It calls no cudaMalloc, cudaFree or allocating
+ * library routine: its intermediates and the sparse MPO blocks live in one
+ * fixed device array of TDVP_NOALLOC_SCRATCH_BYTES bytes inside the library,
+ * present on every GPU that loads it until the process exits. Problems whose
+ * scratch, 2 * chi_l * m * D * chi_r * 16 bytes (D = d^2 for nsite = 2, d for
+ * nsite = 1) plus the MPO blocks, exceeds that size are rejected with
+ * TDVP_EINVAL. The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) and should come before any stream capture. All calls
+ * share the array: calls whose work overlaps on the GPU race on it and must be
+ * serialised by the caller. W is a host pointer; L, R, x, y are device
+ * pointers as in tdvp_op_heff. Synchronises `stream`. */
+#define TDVP_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int tdvp_op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,
+                         const double* R, const double* x, double* y, void* stream);
+
 /* ---- profiling ---- */
 
 /* enable != 0: from now on every kernel launch of the library is bracketed by

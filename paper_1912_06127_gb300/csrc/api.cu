@@ -1366,4 +1366,13 @@ int tdvp_profile_read(int idx, char* name, int name_len, double* ms, int64_t* la
   return rc == TDVP_OK ? n : rc;
 }
 
+int tdvp_op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,
+                         const double* R, const double* x, double* y, void* stream) {
+  return ok_or_code([&] {
+    if (!W || !L || !R || !x || !y) fail(TDVP_EINVAL, "NULL argument");
+    require_device();
+    op_heff_noalloc(nsite, chi_l, chi_r, m, d, W, L, R, x, y, (cudaStream_t)stream);
+  });
+}
+
 }  // extern "C"

@@ -39,6 +39,8 @@ struct ProfScope {
   ~ProfScope();
 };
 void prof_enable(bool on);
+void op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,
+                     const double* R, const double* x, double* y, cudaStream_t s);
 int prof_read(int idx, std::string& name, double& ms, int64_t& launches, double& flops, double& bytes);
 
 // ---------------------------------------------------------------------------

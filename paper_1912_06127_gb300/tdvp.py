@@ -96,6 +96,7 @@ def lib():
                           ctypes.c_int),
         "tdvp_tridiag_expm": ([ctypes.c_int, _D, _D, ctypes.c_double, _D], ctypes.c_int),
         "tdvp_profile": ([ctypes.c_int], ctypes.c_int),
+        "tdvp_op_heff_noalloc": ([ctypes.c_int] * 5 + [_D, _P, _P, _P, _P, _P], ctypes.c_int),
         "tdvp_profile_read": ([ctypes.c_int, ctypes.c_char_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int64),
                                _D, _D], ctypes.c_int),
     }
@@ -297,6 +298,13 @@ def op_heff(precision, nsite, chi_l, chi_r, m, d, W, L, R, x, y, stream=None):
     Wh = np.ascontiguousarray(W, dtype=np.complex128)
     _check(lib().tdvp_op_heff(precision, nsite, chi_l, chi_r, m, d, _dptr(Wh.view(np.float64)), _ptr(L),
                               _ptr(R), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def op_heff_noalloc(nsite, chi_l, chi_r, m, d, W, L, R, x, y, stream=None):
+    """FP64 H_eff . x using only the library's fixed scratch array (no device allocation)."""
+    Wh = np.ascontiguousarray(W, dtype=np.complex128)
+    _check(lib().tdvp_op_heff_noalloc(nsite, chi_l, chi_r, m, d, _dptr(Wh.view(np.float64)), _ptr(L), _ptr(R),
+                                      _ptr(x), _ptr(y), _stream(stream)))
 
 
 def op_env(precision, side, chi_l, chi_r, m, d, W, env, A, out, stream=None):
