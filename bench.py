@@ -357,7 +357,8 @@ def run_ours(args, world, rank, local):
         "roofline": rl,
         "roofline_heff_gemm": rl_heff,
         "heff_tflops": st.heff_flops / max(heff_ms * 1e-3, 1e-12) / 1e12 if heff_ms else None,
-        "kernels": {k: {"ms": v["ms"], "launches": v["launches"], "share": v["ms"] / max(ms, 1e-9)}
+        "kernels": {k: {"ms": v["ms"], "launches": v["launches"], "share": v["ms"] / max(ms, 1e-9),
+                        "aux": v.get("aux", 0.0)}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
         "w_total": st.w_total, "chi_max_seen": st.chi_max_seen, "wall_s": wall,
     }

@@ -222,8 +222,11 @@ int tdvp_op_expm(int precision, int nsite, int chi_l, int chi_r, int m, int d, c
  * Psi_R [chi][cols] = Lambda V^dagger, V [chi] = 1/Lambda, with the rank
  * chosen as in tdvp_step_params. Psi_L / Psi_R must hold min(rows, cols)
  * columns / rows; s_out (device, may be NULL) receives all min(rows, cols)
- * singular values in descending order. chi and w (discarded weight) are
- * written to host ints/doubles. rows, cols <= 4096. */
+ * singular values in descending order. When s_out is NULL the SVD skips the
+ * rotations between vectors that the truncation certainly discards (the
+ * kept triplets, chi and w are unchanged; the discarded directions are not
+ * resolved). chi and w (discarded weight) are written to host ints/doubles.
+ * rows, cols <= 4096. */
 int tdvp_op_split(int rows, int cols, const double* theta, int chi_max, double w_max, double eps,
                   double* Psi_L, double* V, double* Psi_R, double* s_out, int* chi, double* w,
                   void* stream);
@@ -259,6 +262,9 @@ int tdvp_profile(int enable);
  * ms, launches, algorithmic flops and bytes; returns 1. Synchronises. */
 int tdvp_profile_read(int idx, char* name, int name_len, double* ms, int64_t* launches, double* flops,
                       double* bytes);
+/* Auxiliary count accumulated for kind idx (the Jacobi SVD phases: sweeps
+ * summed over the problems of each batch). Returns 1 or an error code. */
+int tdvp_profile_read_aux(int idx, double* aux);
 
 /* ---- host-only utilities (no GPU needed) ---- */
 

@@ -317,6 +317,7 @@ void read_stage_results(tdvp_mps_s* S, int n, cudaStream_t s) {
   if (st & 4) fail(TDVP_ENUMERIC, "tridiagonal eigen-solver did not converge");
   if (st & 16) fail(TDVP_ENUMERIC, "Jacobi SVD did not converge");
   if (st & 32) fail(TDVP_ETIMEOUT, "a bounded grid barrier gave up (SVD sweeps)");
+  if (st & 64) fail(TDVP_ENUMERIC, "SVD tail rule violated: a kept singular value lies below the tail threshold");
 }
 
 struct StageOp {
@@ -1038,6 +1039,7 @@ struct OpCtx {
     if (st & 4) fail(TDVP_ENUMERIC, "tridiagonal eigen-solver did not converge");
     if (st & 16) fail(TDVP_ENUMERIC, "Jacobi SVD did not converge");
     if (st & 32) fail(TDVP_ETIMEOUT, "a bounded grid barrier gave up (SVD sweeps)");
+    if (st & 64) fail(TDVP_ENUMERIC, "SVD tail rule violated: a kept singular value lies below the tail threshold");
   }
 };
 
@@ -1341,18 +1343,18 @@ int tdvp_profile(int enable) {
   });
 }
 
-int tdvp_profile_read(int idx, char* name, int name_len, double* ms, int64_t* launches, double* flops,
-                      double* bytes) {
+static int profile_read_impl(int idx, char* name, int name_len, double* ms, int64_t* launches, double* flops,
+                             double* bytes, double* aux) {
   int n = 0;
   int rc = ok_or_code([&] {
     std::string nm;
-    double t = 0, f = 0, b = 0;
+    double t = 0, f = 0, b = 0, a = 0;
     int64_t l = 0;
     if (idx < 0) {
-      n = prof_read(-1, nm, t, l, f, b);
+      n = prof_read(-1, nm, t, l, f, b, a);
       return;
     }
-    if (!prof_read(idx, nm, t, l, f, b)) fail(TDVP_EINVAL, "profile index out of range");
+    if (!prof_read(idx, nm, t, l, f, b, a)) fail(TDVP_EINVAL, "profile index out of range");
     if (name && name_len > 0) {
       std::strncpy(name, nm.c_str(), name_len - 1);
       name[name_len - 1] = 0;
@@ -1361,9 +1363,19 @@ int tdvp_profile_read(int idx, char* name, int name_len, double* ms, int64_t* la
     if (launches) *launches = l;
     if (flops) *flops = f;
     if (bytes) *bytes = b;
+    if (aux) *aux = a;
     n = 1;
   });
   return rc == TDVP_OK ? n : rc;
+}
+
+int tdvp_profile_read(int idx, char* name, int name_len, double* ms, int64_t* launches, double* flops,
+                      double* bytes) {
+  return profile_read_impl(idx, name, name_len, ms, launches, flops, bytes, nullptr);
+}
+
+int tdvp_profile_read_aux(int idx, double* aux) {
+  return profile_read_impl(idx, nullptr, 0, nullptr, nullptr, nullptr, nullptr, aux);
 }
 
 int tdvp_op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,

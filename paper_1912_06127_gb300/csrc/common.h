@@ -35,13 +35,16 @@ extern bool g_prof_on;
 struct ProfScope {
   int slot = -1;
   cudaStream_t s = 0;
-  ProfScope(const char* name, cudaStream_t s, double flops, double bytes);
+  ProfScope(const char* name, cudaStream_t s, double flops, double bytes, const double* dev_flops_host = nullptr);
   ~ProfScope();
 };
 void prof_enable(bool on);
+// two doubles: [0] work (flops) and [1] an auxiliary count, written by the kernel
+double* prof_work_slot(double** dev);
 void op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,
                      const double* R, const double* x, double* y, cudaStream_t s);
-int prof_read(int idx, std::string& name, double& ms, int64_t& launches, double& flops, double& bytes);
+int prof_read(int idx, std::string& name, double& ms, int64_t& launches, double& flops, double& bytes,
+              double& aux);
 
 // ---------------------------------------------------------------------------
 // Complex helpers (double2 / float2 hold re, im)

@@ -31,7 +31,7 @@ struct DeviceWOp {
 
 // Workspace of one local problem of a batch.
 struct Slot {
-  int64_t cap_vec = 0, cap_T = 0, cap_f = 0;
+  int64_t cap_vec = 0, cap_T = 0, cap_f = 0, cap_svd = 0;
   int kmax = 0;
   double2* theta = nullptr;   // two-site state Theta
   double2* theta2 = nullptr;  // evolved state

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(LZ_THREADS) lz_start_scale(const __grid_consta
 }
 
 // ---- pass: coefficients <v_i, w> for i <= j --------------------------------
+template <int NMAX>
 __global__ void __launch_bounds__(LZ_THREADS) lz_dots(const __grid_constant__ LzBatch B, int j,
                                                       int pass) {
   const LzDesc& P = B.d[blockIdx.y];
@@ -132,11 +133,12 @@ __global__ void __launch_bounds__(LZ_THREADS) lz_dots(const __grid_constant__ Lz
   if ((int)blockIdx.x >= nblk) return;
   __shared__ double2 scratch[(LZ_THREADS / 32) * KRYLOV_MAX];
   __shared__ double2 tot[KRYLOV_MAX];
-  // accumulators indexed by compile-time constants only (registers, no local memory)
-  double2 acc[KRYLOV_MAX];
+  // accumulators indexed by compile-time constants only (registers, no local
+  // memory); NMAX >= j + 1 is chosen at launch
+  double2 acc[NMAX];
   const int cnt = j + 1;
 #pragma unroll
-  for (int i = 0; i < KRYLOV_MAX; ++i) acc[i] = make_double2(0, 0);
+  for (int i = 0; i < NMAX; ++i) acc[i] = make_double2(0, 0);
   const double2* w = P.V + (int64_t)(j + 1) * P.vs;
   const int64_t base = (int64_t)blockIdx.x * LZ_THREADS * LZ_ELEMS;
   for (int e = 0; e < LZ_ELEMS; ++e) {
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(LZ_THREADS) lz_dots(const __grid_constant__ Lz
     if (idx >= P.n) break;
     double2 wv = w[idx];
 #pragma unroll
-    for (int i = 0; i < KRYLOV_MAX; ++i)
+    for (int i = 0; i < NMAX; ++i)
       if (i < cnt) zfma_cj(acc[i], P.V[(int64_t)i * P.vs + idx], wv);
   }
   block_sum(acc, cnt, scratch, tot);
@@ -290,7 +292,9 @@ void lz_orthogonalize(const LzBatch& b, int j, cudaStream_t s) {
   ProfScope ps("lanczos_orth", s, 2.0 * 2 * 8.0 * (j + 1) * n_all,
                16.0 * n_all * (2.0 * ((j + 2) + (j + 3)) + 2.0));
   for (int pass = 0; pass < 2; ++pass) {
-    lz_dots<<<lz_grid(b, true), LZ_THREADS, 0, s>>>(b, j, pass);
+    if (j + 1 <= 8) lz_dots<8><<<lz_grid(b, true), LZ_THREADS, 0, s>>>(b, j, pass);
+    else if (j + 1 <= 16) lz_dots<16><<<lz_grid(b, true), LZ_THREADS, 0, s>>>(b, j, pass);
+    else lz_dots<KRYLOV_MAX><<<lz_grid(b, true), LZ_THREADS, 0, s>>>(b, j, pass);
     LAUNCH_CHECK();
     lz_update<<<lz_grid(b, true), LZ_THREADS, 0, s>>>(b, j, pass);
     LAUNCH_CHECK();

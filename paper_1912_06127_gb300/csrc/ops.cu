@@ -104,10 +104,13 @@ int64_t mixed_cap_floats(int chi, int m, int d) {
 }
 
 void Slot::ensure(int64_t vec, int64_t T, int64_t fsz, int64_t svd_n, int kmax_) {
-  if (vec <= cap_vec && T <= cap_T && fsz <= cap_f && kmax_ <= kmax && svd_n * svd_n <= (svdX ? cap_vec : 0))
+  if (vec <= cap_vec && T <= cap_T && fsz <= cap_f && kmax_ <= kmax && svd_n <= cap_svd &&
+      svd_n * svd_n <= (svdX ? cap_vec : 0))
     return;
+  const int64_t nsvd = std::max(svd_n, cap_svd);
   release();
-  cap_vec = std::max(vec, svd_n * svd_n);
+  cap_svd = nsvd;
+  cap_vec = std::max(vec, nsvd * nsvd);
   cap_T = T;
   cap_f = fsz;
   kmax = kmax_;
@@ -132,8 +135,8 @@ void Slot::ensure(int64_t vec, int64_t T, int64_t fsz, int64_t svd_n, int kmax_)
   svdAcc32 = dalloc<float2>(cap_vec);
   maxr = reinterpret_cast<unsigned*>(dalloc<int>(1));
   sync = reinterpret_cast<unsigned*>(dalloc<int>(4));
-  sig = dalloc<double>(svd_n + 2);
-  perm = dalloc<int>(svd_n + 1);
+  sig = dalloc<double>(nsvd + 3);
+  perm = dalloc<int>(nsvd + 1);
   rot = dalloc<int>(1);
   conv = dalloc<int>(1);
 }
@@ -155,7 +158,7 @@ void Slot::release() {
   st = nullptr;
   counter = perm = rot = conv = nullptr;
   sig = nullptr;
-  cap_vec = cap_T = cap_f = 0;
+  cap_vec = cap_T = cap_f = cap_svd = 0;
   kmax = 0;
 }
 

@@ -19,7 +19,11 @@
 // the job. Cyclic Jacobi converges quadratically, so a sweep whose largest
 // relative off-diagonal |<x,y>|/(|x||y|) stayed below 1e-7 leaves less than
 // ~1e-14 and ends the iteration. The result has FP64 accuracy; the FP32
-// phase only shortens the FP64 phase.
+// phase only shortens the FP64 phase. The FP64 phase skips pairs of vectors
+// that both lie below a threshold under which the truncation discards
+// everything (svd_tail_threshold): such rotations change neither the kept
+// vectors nor the discarded weight, and without them the FP64 phase needs no
+// more sweeps for the tail than for the kept part.
 //
 // Truncation (Sec. III C, Eq. 22 and Sec. III D): the smallest rank chi_w
 // whose discarded weight sum_{j >= chi_w} lambda_j^2 is <= w_max, capped at
@@ -116,6 +120,8 @@ struct Prec<double2> {
   static constexpr double tol = JACOBI_TOL;
   // pairs whose norms are both below 1e-14 ||theta||_F are rounding noise
   __device__ static R zero_level(const SvdDesc& P) { return 1e-28 * P.sig[P.n_vec + 1]; }
+  // the FP64 phase tracks the vector norms in sig[0, n_vec) for the tail rule
+  static constexpr bool tracks_norms = true;
   __device__ static R wsum(R v) { return warp_sum(v); }
   __device__ static double2* X(const SvdDesc& P) { return P.X; }
   __device__ static double2* Acc(const SvdDesc& P) { return P.Acc; }
@@ -130,6 +136,7 @@ struct Prec<float2> {
     const double sc = P.sig[P.n_vec];
     return (R)(1e-12 * P.sig[P.n_vec + 1] * sc * sc);
   }
+  static constexpr bool tracks_norms = false;
   __device__ static R wsum(R v) { return warp_sumf(v); }
   __device__ static float2* X(const SvdDesc& P) { return P.X32; }
   __device__ static float2* Acc(const SvdDesc& P) { return P.Acc32; }
@@ -184,10 +191,10 @@ __device__ inline void rot_rows_regs(T* x, T* y, int n, int lane, typename Prec<
 template <typename T>
 __device__ inline bool jacobi_params(const SvdDesc& P, typename Prec<T>::R a, typename Prec<T>::R b,
                                      typename Prec<T>::R kr, typename Prec<T>::R ki, int lane,
-                                     typename Prec<T>::R& cs, T& m1, T& m2) {
+                                     typename Prec<T>::R& cs, T& m1, T& m2, typename Prec<T>::R& tk) {
   using R = typename Prec<T>::R;
   const R ak = sqrt(kr * kr + ki * ki);
-  const R ab = sqrt(a * b);
+  const R ab = sqrt(a) * sqrt(b);  // not sqrt(a b): a b can underflow in FP32
   if (!(ak > Prec<T>::tol * ab)) return false;
   // a vector at rounding-noise level has a noise direction: leave it alone
   // (such values are dropped by the truncation's noise floor)
@@ -201,6 +208,7 @@ __device__ inline bool jacobi_params(const SvdDesc& P, typename Prec<T>::R a, ty
   const R t = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
   cs = R(1) / sqrt(R(1) + t * t);
   const R sn = cs * t;
+  tk = t * ak;  // the norms become a - t|k| and b + t|k|
   // x' = cs x - sn e^{-i phi} y ; y' = sn e^{i phi} x + cs y
   m1 = Prec<T>::mk(-sn * phr, sn * phi);
   m2 = Prec<T>::mk(sn * phr, sn * phi);
@@ -230,14 +238,21 @@ __device__ inline void jacobi_pair(const SvdDesc& P, int r, int pair, int lane) 
     q = t;
   }
   if (q >= P.n_vec) return;
+  if constexpr (Prec<T>::tracks_norms) {
+    // tail rule: two vectors that both stay below the truncation threshold
+    // need not be orthogonalised against each other (see svd_tail_threshold)
+    const double tau = P.sig[P.n_vec + 2];
+    if (tau > 0.0 && P.sig[p] < tau && P.sig[q] < tau) return;
+  }
   T* X = Prec<T>::X(P);
   T* x = X + (int64_t)p * P.len;
   T* y = X + (int64_t)q * P.len;
   T* A = Prec<T>::Acc(P);
   T* ax = A + (int64_t)p * P.n_vec;
   T* ay = A + (int64_t)q * P.n_vec;
-  R cs;
+  R cs, tk;
   T m1, m2;
+  R a = 0, b = 0, kr = 0, ki = 0;
   if (P.len <= 32 * NR) {
     T u[NR], v[NR];
 #pragma unroll
@@ -246,7 +261,6 @@ __device__ inline void jacobi_pair(const SvdDesc& P, int r, int pair, int lane) 
       u[e] = i < P.len ? x[i] : Prec<T>::mk(0, 0);
       v[e] = i < P.len ? y[i] : Prec<T>::mk(0, 0);
     }
-    R a = 0, b = 0, kr = 0, ki = 0;
 #pragma unroll
     for (int e = 0; e < NR; ++e) {
       a += u[e].x * u[e].x + u[e].y * u[e].y;
@@ -258,7 +272,7 @@ __device__ inline void jacobi_pair(const SvdDesc& P, int r, int pair, int lane) 
     b = Prec<T>::wsum(b);
     kr = Prec<T>::wsum(kr);
     ki = Prec<T>::wsum(ki);
-    if (!jacobi_params<T>(P, a, b, kr, ki, lane, cs, m1, m2)) return;
+    if (!jacobi_params<T>(P, a, b, kr, ki, lane, cs, m1, m2, tk)) return;
     rot_regs<T, NR>(u, v, cs, m1, m2);
 #pragma unroll
     for (int e = 0; e < NR; ++e) {
@@ -269,7 +283,6 @@ __device__ inline void jacobi_pair(const SvdDesc& P, int r, int pair, int lane) 
       }
     }
   } else {
-    R a = 0, b = 0, kr = 0, ki = 0;
     for (int i = lane; i < P.len; i += 32) {
       T u = x[i], v = y[i];
       a += u.x * u.x + u.y * u.y;
@@ -281,8 +294,15 @@ __device__ inline void jacobi_pair(const SvdDesc& P, int r, int pair, int lane) 
     b = Prec<T>::wsum(b);
     kr = Prec<T>::wsum(kr);
     ki = Prec<T>::wsum(ki);
-    if (!jacobi_params<T>(P, a, b, kr, ki, lane, cs, m1, m2)) return;
+    if (!jacobi_params<T>(P, a, b, kr, ki, lane, cs, m1, m2, tk)) return;
     rot2<T>(x, y, P.len, lane, cs, m1, m2);
+  }
+  if constexpr (Prec<T>::tracks_norms) {
+    // no other warp touches p or q in this round
+    if (lane == 0) {
+      P.sig[p] = sqrt(fmax((double)(a - tk), 0.0));
+      P.sig[q] = sqrt((double)(b + tk));
+    }
   }
   if (P.n_vec <= 32 * NR) rot_rows_regs<T, NR>(ax, ay, P.n_vec, lane, cs, m1, m2);
   else rot2<T>(ax, ay, P.n_vec, lane, cs, m1, m2);
@@ -329,6 +349,95 @@ __device__ inline bool grid_barrier(unsigned* sync, unsigned nblocks, int* statu
   return ok_sh != 0;
 }
 
+// Tail rule of the FP64 phase. After the FP32 phase the vectors are mutually
+// orthogonal to FP32 accuracy and their norms nu_i approximate the singular
+// values. The truncation keeps at most k* of them (k* computed below from the
+// nu with safety margins), so every vector whose norm stays below
+// tau = nu_(k*) / 2 is discarded. A rotation between two such vectors changes
+// neither the kept vectors nor the discarded weight (it conserves the sum of
+// their squared norms), so the FP64 phase skips those pairs and orthogonalises
+// every other pair to FP64 accuracy: all vectors above tau end as singular
+// vectors of the FP64 iterate. A vector below tau only shrinks in a rotation
+// with a larger partner, so it stays below. k* over-estimates the final rank:
+// tail sums of the nu^2 (the diagonal of a unitary transform of Theta Theta^H,
+// majorised by the sigma^2) over-estimate the true ones, the weight test uses
+// w_max / 4 and the eps and noise tests half their thresholds. svd_truncate
+// flags (status bit 64) a kept value below tau; the sweeps check the rule at
+// convergence and drop it (tau = 0) if it failed.
+// tau = 0 (no skipping) when the whole spectrum is returned.
+constexpr int SVD_TAIL_MAX = 6144;  // vectors; the sorted norms live in shared memory
+__global__ void svd_tail_threshold(const __grid_constant__ SvdBatch B) {
+  extern __shared__ double srt[];
+  __shared__ int has_nan;
+  const SvdDesc& P = B.d[blockIdx.x];
+  const int n = P.n_vec;
+  if (P.s_sorted != nullptr || n > SVD_TAIL_MAX) {
+    if (threadIdx.x == 0) P.sig[n + 2] = 0.0;
+    return;
+  }
+  if (threadIdx.x == 0) has_nan = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double si = P.sig[i];
+    if (!(si == si)) has_nan = 1;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double sj = P.sig[j];
+      rank += (sj > si) || (sj == si && j < i);
+    }
+    if (rank < n) srt[rank] = si;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double tau = 0.0;
+  if (!has_nan && srt[0] > 0.0) {
+    const double s0 = srt[0];
+    int kw = n;  // smallest k >= 1 with sum_{j >= k} nu_j^2 <= w_max / 4
+    double acc = 0.0;
+    for (int k = n - 1; k >= 1; --k) {
+      acc += srt[k] * srt[k];
+      if (acc <= 0.25 * P.w_max) kw = k;
+      else break;
+    }
+    const double thr = 0.5 * fmax(P.eps * s0, 1e-14 * sqrt(P.sig[n + 1]));
+    int ne = 0;
+    for (int k = 0; k < n; ++k) ne += srt[k] > thr;
+    int ks = kw < P.chi_max ? kw : P.chi_max;
+    if (ne < ks) ks = ne;
+    if (ks < 1) ks = 1;
+    // only where the FP32 phase resolved the norms: well above its noise
+    // level (vectors below 1e-6 ||theta||_F are not rotated there)
+    if (ks < n && 0.5 * srt[ks] >= 1e-5 * sqrt(P.sig[n + 1])) tau = 0.5 * srt[ks];
+  }
+  P.sig[n + 2] = tau;
+}
+
+// Whether the tail rule held at convergence: the truncation keeps only vectors
+// above tau (at least chi_max of them lie above it, or every vector below it
+// fails the eps / noise test, or their squared norms sum to at most w_max --
+// the three ways svd_truncate can stop before reaching them). Uses the norms
+// tracked by the sweeps. One thread.
+__device__ inline bool svd_tail_rule_holds(const SvdDesc& P) {
+  const int n = P.n_vec;
+  const double tau = P.sig[n + 2];
+  if (!(tau > 0.0)) return true;
+  int cnt = 0;
+  double s0 = 0.0, below_max = 0.0, below_w = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double si = P.sig[i];
+    s0 = fmax(s0, si);
+    if (si >= tau) {
+      ++cnt;
+    } else {
+      below_max = fmax(below_max, si);
+      below_w += si * si;
+    }
+  }
+  if (cnt >= P.chi_max) return true;
+  const double thr = fmax(P.eps * s0, 1e-14 * sqrt(P.sig[n + 1]));
+  return below_max <= thr || below_w <= P.w_max;
+}
+
 // All sweeps of one phase in one cooperative launch: rounds separated by grid
 // barriers, warps striding over the pairs of all problems; after each sweep
 // block 0 marks converged problems (no rotation, or the largest relative
@@ -336,7 +445,8 @@ __device__ inline bool grid_barrier(unsigned* sync, unsigned nblocks, int* statu
 // sync[2] = unconverged count of the last sweep.
 template <typename T>
 __global__ void __launch_bounds__(SVD_WARPS * 32) svd_sweeps(const __grid_constant__ SvdBatch B, int npad_max,
-                                                            float stop, int max_sweeps) {
+                                                            float stop, int max_sweeps, int fatal,
+                                                            double* work_flops) {
   __shared__ int off[MAXB + 1];
   if (threadIdx.x == 0) {
     off[0] = 0;
@@ -368,19 +478,34 @@ __global__ void __launch_bounds__(SVD_WARPS * 32) svd_sweeps(const __grid_consta
       for (int i = 0; i < B.n; ++i) {
         const SvdDesc& P = B.d[i];
         if (!*P.conv) {
-          if (*P.rotated == 0 || __uint_as_float(*P.maxr) < stop) *P.conv = 1;
+          // work of this sweep: every pair's dots, and the rotations applied
+          if (work_flops) {
+            const double pairs = 0.5 * P.n_vec * (P.n_vec - 1);
+            work_flops[0] += 16.0 * P.len * pairs + 20.0 * (P.len + P.n_vec) * (double)*P.rotated;
+            work_flops[1] += 1.0;  // sweeps, summed over the problems of the batch
+          }
+          bool done = *P.rotated == 0 || __uint_as_float(*P.maxr) < stop;
+          if constexpr (Prec<T>::tracks_norms) {
+            // the estimate behind the tail rule failed: drop the rule and
+            // sweep on until every pair is orthogonal
+            if (done && !svd_tail_rule_holds(P)) {
+              P.sig[P.n_vec + 2] = 0.0;
+              done = false;
+            }
+          }
+          if (done) *P.conv = 1;
           else ++cnt;
         }
         *P.rotated = 0;
         *P.maxr = 0u;
       }
       *unconv = cnt;
-      __threadfence();
+      __threadfence_system();
     }
     if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
     if (*unconv == 0) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, 16);
+  if (fatal && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, 16);
 }
 
 // FP32 rotation -> FP64; reset the convergence state for the FP64 phase
@@ -483,6 +608,9 @@ __global__ void svd_truncate(const __grid_constant__ SvdBatch B) {
     const double sk = P.sig[P.perm[k]];
     tail += sk * sk;
   }
+  // the tail rule left the vectors below tau unconverged among themselves
+  const double tau = P.sig[n + 2];
+  if (tau > 0.0 && P.sig[P.perm[chi - 1]] < tau) atomicOr(B.status, 64);
   *P.chi = chi;
   *P.w = tail;
 }
@@ -518,10 +646,10 @@ __global__ void svd_write(const __grid_constant__ SvdBatch B) {
   }
 }
 
-// all sweeps of one phase as one cooperative launch (no host round trips)
+// all sweeps of one phase as one cooperative launch (no host round trips);
+// `fatal`: running out of sweeps is an error (FP64 phase) or not (FP32 phase)
 template <typename T>
-static void jacobi_sweeps(SvdBatch& b, int npad_max, float stop, cudaStream_t s, const char* name,
-                          double flops_per_sweep) {
+static void jacobi_sweeps(SvdBatch& b, int npad_max, float stop, int fatal, cudaStream_t s, const char* name) {
   static int max_blocks = -1;
   if (max_blocks < 0) {
     int dev = 0, sms = 0, per_sm = 0;
@@ -535,8 +663,10 @@ static void jacobi_sweeps(SvdBatch& b, int npad_max, float stop, cudaStream_t s,
   const int blocks = std::max(1, std::min(max_blocks, cdiv(total, SVD_WARPS)));
   CUDA_TRY(cudaMemsetAsync(b.sync, 0, 4 * sizeof(unsigned), s));
   int max_sweeps = SVD_MAX_SWEEPS;
-  void* args[] = {(void*)&b, (void*)&npad_max, (void*)&stop, (void*)&max_sweeps};
-  ProfScope ps(name, s, flops_per_sweep, 0.0);
+  double* work_dev = nullptr;
+  const double* work_host = prof_work_slot(&work_dev);
+  void* args[] = {(void*)&b, (void*)&npad_max, (void*)&stop, (void*)&max_sweeps, (void*)&fatal, (void*)&work_dev};
+  ProfScope ps(name, s, 0.0, 0.0, work_host);
   CUDA_TRY(cudaLaunchCooperativeKernel((const void*)svd_sweeps<T>, dim3(blocks), dim3(SVD_WARPS * 32), args, 0, s));
   ++g_launches;
 }
@@ -545,7 +675,6 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   if (b.n <= 0) return;
   int64_t max_elems = 1;
   int npad_max = 2, nvec_max = 1;
-  double fl = 0;
   for (int i = 0; i < b.n; ++i) {
     auto& P = b.d[i];
     P.trans = P.rows > P.cols ? 1 : 0;
@@ -554,8 +683,6 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
     max_elems = std::max<int64_t>(max_elems, (int64_t)P.n_vec * (P.len + P.n_vec));
     npad_max = std::max(npad_max, P.n_vec + (P.n_vec & 1));
     nvec_max = std::max(nvec_max, P.n_vec);
-    // dots of every pair once per sweep (lower bound of the sweep's work)
-    fl += 16.0 * (double)P.len * (P.n_vec / 2) * (P.n_vec - 1);
   }
   dim3 g1((unsigned)std::min<int64_t>(cdiv64(max_elems, 256), 152 * 8), b.n);
   // ---- phase 1: FP32 sweeps ----
@@ -564,7 +691,10 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   svd_setup32<<<g1, 256, 0, s>>>(b);
   LAUNCH_CHECK();
   ++g_launches;
-  jacobi_sweeps<float2>(b, npad_max, 1e-3f, s, "svd_jacobi_fp32", fl);
+  // FP32 phase: until the largest relative off-diagonal of a sweep is < 1e-4
+  // (just above the FP32 rounding of the dot products); not converging here
+  // only means a weaker preconditioner
+  jacobi_sweeps<float2>(b, npad_max, 1e-4f, 0, s, "svd_jacobi_fp32");
   // ---- phase 2: unitary FP64 rotation and FP64 vectors ----
   svd_acc_to64<<<g1, 256, 0, s>>>(b);
   LAUNCH_CHECK();
@@ -607,10 +737,16 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   launch_zgemm(gx, s, "svd_newton_schulz");
   g_launches += 2;
   // ---- phase 3: FP64 sweeps ----
-  // stop after a sweep whose largest relative off-diagonal was below 1e-7 (full:
-  // ~1e-14 left) or 1e-5 (mixed-precision sweeps: ~1e-10 or less left)
-  jacobi_sweeps<double2>(b, npad_max, b.mode == 0 ? 1e-7f : 1e-5f, s, "svd_jacobi_fp64", fl);
   dim3 gn(cdiv(nvec_max, SVD_WARPS), b.n);
+  svd_norms<<<gn, SVD_WARPS * 32, 0, s>>>(b);
+  LAUNCH_CHECK();
+  const size_t tail_smem = nvec_max <= SVD_TAIL_MAX ? (size_t)nvec_max * sizeof(double) : 0;
+  svd_tail_threshold<<<b.n, 256, tail_smem, s>>>(b);
+  LAUNCH_CHECK();
+  g_launches += 2;
+  // stop after a sweep whose largest relative off-diagonal was below 1e-7 (full:
+  // ~1e-14 left) or 1e-4 (mixed-precision sweeps: ~1e-8 or less left)
+  jacobi_sweeps<double2>(b, npad_max, b.mode == 0 ? 1e-7f : 1e-4f, 1, s, "svd_jacobi_fp64");
   svd_norms<<<gn, SVD_WARPS * 32, 0, s>>>(b);
   LAUNCH_CHECK();
   svd_truncate<<<b.n, 256, 0, s>>>(b);

@@ -16,7 +16,7 @@ struct SvdDesc {
   double2* P;            // [n_vec][n_vec] Newton-Schulz temporaries
   double2* T;
   unsigned* maxr;        // largest |<x,y>| / (|x| |y|) met in the current sweep (float bits)
-  double* sig;           // [n_vec + 2] norms of the final vectors, then scale and ||theta||_F^2
+  double* sig;           // [n_vec + 3] vector norms, then scale, ||theta||_F^2 and the tail threshold
   int* perm;             // [n_vec] descending order
   int* rotated;          // rotations applied in the current sweep
   int* conv;             // 1 once a sweep applied no rotation
@@ -31,16 +31,17 @@ struct SvdDesc {
 };
 struct SvdBatch {
   int n;
-  int mode;              // 0: FP64 to ~1e-14 orthogonality; 1: to ~1e-12 (mixed-precision sweeps)
-  int* status;           // bit 8: NaN / zero state, bit 16: no convergence, bit 32: barrier timeout
+  int mode;              // 0: FP64 to ~1e-14 orthogonality; 1: to ~1e-8 or better (mixed-precision sweeps)
+  int* status;           // bit 8: NaN / zero state, 16: no convergence, 32: barrier timeout, 64: tail rule
   unsigned* sync;        // 4 words of device scratch for the grid barrier and the sweep loop
   SvdDesc d[MAXB];
 };
 
 // Full pipeline: FP32 Jacobi sweeps (preconditioner), Newton-Schulz
 // re-orthonormalisation of the accumulated rotation and recomputation of the
-// vectors in FP64, FP64 Jacobi sweeps until converged (one host
-// synchronisation per sweep), then sort, truncate and write Psi_L, V, Psi_R.
+// vectors in FP64, FP64 Jacobi sweeps until converged (pairs of vectors that
+// the truncation certainly discards are skipped), then sort, truncate and
+// write Psi_L, V, Psi_R.
 // h_flag: pinned host int.
 void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s);
 

@@ -96,6 +96,7 @@ def lib():
                           ctypes.c_int),
         "tdvp_tridiag_expm": ([ctypes.c_int, _D, _D, ctypes.c_double, _D], ctypes.c_int),
         "tdvp_profile": ([ctypes.c_int], ctypes.c_int),
+        "tdvp_profile_read_aux": ([ctypes.c_int, _D], ctypes.c_int),
         "tdvp_op_heff_noalloc": ([ctypes.c_int] * 5 + [_D, _P, _P, _P, _P, _P], ctypes.c_int),
         "tdvp_profile_read": ([ctypes.c_int, ctypes.c_char_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int64),
                                _D, _D], ctypes.c_int),
@@ -363,5 +364,8 @@ def profile_read() -> dict:
         la = ctypes.c_int64()
         _check(lib().tdvp_profile_read(i, name, 64, ctypes.byref(ms), ctypes.byref(la), ctypes.byref(fl),
                                        ctypes.byref(by)))
-        out[name.value.decode()] = {"ms": ms.value, "launches": la.value, "flops": fl.value, "bytes": by.value}
+        aux = ctypes.c_double()
+        _check(lib().tdvp_profile_read_aux(i, ctypes.byref(aux)))
+        out[name.value.decode()] = {"ms": ms.value, "launches": la.value, "flops": fl.value, "bytes": by.value,
+                                    "aux": aux.value}
     return out

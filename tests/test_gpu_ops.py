@@ -211,6 +211,56 @@ def test_split_rank_deficient(eps, rows, cols):
     assert np.abs(B @ B.conj().T - np.eye(chi)).max() < 1e-12
 
 
+def gapped_matrix(n, n_big, seed, deg=1):
+    """Spectrum of an evolved two-site state: n_big values from 1 down to 6.5e-3
+    (the previous bond's Schmidt values), then a tail from 7e-4 down to 4e-6
+    (weight the time step moved into new directions); deg > 1 repeats each
+    value deg times (symmetry multiplets)."""
+    U = np.linalg.qr(I.random_complex((n, n), seed))[0]
+    Vh = np.linalg.qr(I.random_complex((n, n), seed + 1))[0]
+    big = np.repeat(np.geomspace(1.0, 6.5e-3, n_big // deg), deg)
+    tail = np.repeat(np.geomspace(7e-4, 4e-6, (n - n_big) // deg), deg)
+    s = np.concatenate([big, tail])
+    return (U * s) @ Vh, s
+
+
+@pytest.mark.parametrize("n,chi_max,w_max,deg", [(160, 80, 0.0, 1), (160, 80, 0.0, 2), (160, 86, 0.0, 1),
+                                                  (160, 200, 1e-9, 1), (96, 200, 0.0, 1)])
+def test_split_tail_rule(n, chi_max, w_max, deg):
+    """Without s_out the SVD skips rotations between vectors that the truncation
+    discards; the kept triplets, chi and the discarded weight must not change."""
+    torch = torch_or_skip()
+    tdvp = lib()
+    theta, _ = gapped_matrix(n, n // 2, 90 + deg, deg)
+    s_ref = np.linalg.svd(theta, compute_uv=False)
+    chi_ref, w_ref = T.truncation_rank(s_ref, chi_max, w_max, 1e-12)
+    outs = []
+    for with_s in (False, True):
+        PsiL = torch.zeros(n * n, dtype=torch.complex128, device="cuda")
+        PsiR = torch.zeros(n * n, dtype=torch.complex128, device="cuda")
+        V = torch.zeros(n, dtype=torch.float64, device="cuda")
+        s = torch.zeros(n, dtype=torch.float64, device="cuda") if with_s else None
+        chi, w = tdvp.op_split(n, n, dev(torch, theta), chi_max, w_max, 1e-12, PsiL, V, PsiR, s)
+        assert chi == chi_ref
+        # singular values agree to ~1e-15 s_1 (absolute): bound on the sum of squares
+        assert abs(w - w_ref) <= 1e-12 * w_ref + 2e-15 * s_ref[0] * np.sqrt(n * w_ref) + 1e-28
+        v = V.cpu().numpy()[:chi]
+        assert np.allclose(1.0 / v, s_ref[:chi], rtol=1e-12, atol=1e-13 * s_ref[0])
+        pl = host(PsiL)[: n * chi].reshape(n, chi)
+        pr = host(PsiR)[: chi * n].reshape(chi, n)
+        A = pl * v[None, :]
+        B = v[:, None] * pr
+        assert np.abs(A.conj().T @ A - np.eye(chi)).max() < 1e-12
+        assert np.abs(B @ B.conj().T - np.eye(chi)).max() < 1e-12
+        rec = (pl * v[None, :]) @ pr
+        outs.append(rec)
+        if deg == 1:  # a unique best rank-chi approximation
+            U, sv, Vh = np.linalg.svd(theta)
+            best = (U[:, :chi] * sv[:chi]) @ Vh[:chi]
+            assert np.abs(rec - best).max() < 1e-12
+    assert np.abs(outs[0] - outs[1]).max() < 1e-12
+
+
 @pytest.mark.parametrize("prec", [FP64, TF32X3], ids=["fp64", "tf32x3"])
 def test_heff_full_size_sampled(prec):
     """H_eff at the chi = 256, m = 10 (N = 101 Ising, 8 exponentials) size of the
