@@ -187,11 +187,13 @@ __device__ inline void rot_rows_regs(T* x, T* y, int n, int lane, typename Prec<
   }
 }
 
-// Rotation parameters of a pair from its Gram entries; false if no rotation.
+// Rotation parameters of a pair from its Gram entries a = |x|^2, b = |y|^2,
+// k = kr + i ki = <x, y>; false if the pair needs no rotation. `ratio`
+// receives |k| / (|x| |y|), `tk` the norm change (|x|^2 -> a - tk, |y|^2 -> b + tk).
 template <typename T>
-__device__ inline bool jacobi_params(const SvdDesc& P, typename Prec<T>::R a, typename Prec<T>::R b,
-                                     typename Prec<T>::R kr, typename Prec<T>::R ki, int lane,
-                                     typename Prec<T>::R& cs, T& m1, T& m2, typename Prec<T>::R& tk) {
+__device__ inline bool jacobi_rotation(const SvdDesc& P, typename Prec<T>::R a, typename Prec<T>::R b,
+                                       typename Prec<T>::R kr, typename Prec<T>::R ki, typename Prec<T>::R& cs,
+                                       T& m1, T& m2, typename Prec<T>::R& tk, float& ratio) {
   using R = typename Prec<T>::R;
   const R ak = sqrt(kr * kr + ki * ki);
   const R ab = sqrt(a) * sqrt(b);  // not sqrt(a b): a b can underflow in FP32
@@ -199,19 +201,30 @@ __device__ inline bool jacobi_params(const SvdDesc& P, typename Prec<T>::R a, ty
   // a vector at rounding-noise level has a noise direction: leave it alone
   // (such values are dropped by the truncation's noise floor)
   if (a < Prec<T>::zero_level(P) || b < Prec<T>::zero_level(P)) return false;
-  if (lane == 0) {
-    atomicAdd(P.rotated, 1);
-    atomicMax(P.maxr, __float_as_uint((float)(ak / ab)));
-  }
+  ratio = (float)(ak / ab);
   const R phr = kr / ak, phi = ki / ak;  // e^{i phi}
   const R zeta = (b - a) / (R(2) * ak);
   const R t = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
   cs = R(1) / sqrt(R(1) + t * t);
   const R sn = cs * t;
-  tk = t * ak;  // the norms become a - t|k| and b + t|k|
+  tk = t * ak;
   // x' = cs x - sn e^{-i phi} y ; y' = sn e^{i phi} x + cs y
   m1 = Prec<T>::mk(-sn * phr, sn * phi);
   m2 = Prec<T>::mk(sn * phr, sn * phi);
+  return true;
+}
+
+// jacobi_rotation plus the convergence bookkeeping of the sweep (lane 0)
+template <typename T>
+__device__ inline bool jacobi_params(const SvdDesc& P, typename Prec<T>::R a, typename Prec<T>::R b,
+                                     typename Prec<T>::R kr, typename Prec<T>::R ki, int lane,
+                                     typename Prec<T>::R& cs, T& m1, T& m2, typename Prec<T>::R& tk) {
+  float ratio = 0.f;
+  if (!jacobi_rotation<T>(P, a, b, kr, ki, cs, m1, m2, tk, ratio)) return false;
+  if (lane == 0) {
+    atomicAdd(P.rotated, 1);
+    atomicMax(P.maxr, __float_as_uint(ratio));
+  }
   return true;
 }
 
@@ -364,33 +377,46 @@ __device__ inline bool grid_barrier(unsigned* sync, unsigned nblocks, int* statu
 // w_max / 4 and the eps and noise tests half their thresholds. svd_truncate
 // flags (status bit 64) a kept value below tau; the sweeps check the rule at
 // convergence and drop it (tau = 0) if it failed.
-// tau = 0 (no skipping) when the whole spectrum is returned.
+// tau = 0 (no skipping) when the whole spectrum is returned. Also writes the
+// order of decreasing norm to perm (the FP64 block sweeps group the vectors
+// in that order, so that the tail forms whole blocks).
 constexpr int SVD_TAIL_MAX = 6144;  // vectors; the sorted norms live in shared memory
 __global__ void svd_tail_threshold(const __grid_constant__ SvdBatch B) {
   extern __shared__ double srt[];
   __shared__ int has_nan;
   const SvdDesc& P = B.d[blockIdx.x];
   const int n = P.n_vec;
-  if (P.s_sorted != nullptr || n > SVD_TAIL_MAX) {
+  if (n > SVD_TAIL_MAX) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) P.perm[i] = i;
     if (threadIdx.x == 0) P.sig[n + 2] = 0.0;
     return;
   }
   if (threadIdx.x == 0) has_nan = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    P.perm[i] = i;
+    if (!(P.sig[i] == P.sig[i])) has_nan = 1;
+  }
+  __syncthreads();
+  if (has_nan) {
+    if (threadIdx.x == 0) P.sig[n + 2] = 0.0;
+    return;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double si = P.sig[i];
-    if (!(si == si)) has_nan = 1;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
       const double sj = P.sig[j];
       rank += (sj > si) || (sj == si && j < i);
     }
-    if (rank < n) srt[rank] = si;
+    srt[rank] = si;
+    P.perm[rank] = i;  // the block sweeps visit the vectors in this order
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
   double tau = 0.0;
-  if (!has_nan && srt[0] > 0.0) {
+  if (srt[0] > 0.0 && P.s_sorted == nullptr) {
     const double s0 = srt[0];
     int kw = n;  // smallest k >= 1 with sum_{j >= k} nu_j^2 <= w_max / 4
     double acc = 0.0;
@@ -438,6 +464,41 @@ __device__ inline bool svd_tail_rule_holds(const SvdDesc& P) {
   return below_max <= thr || below_w <= P.w_max;
 }
 
+// End of a sweep (one thread): marks the problems whose sweep applied no
+// rotation or whose largest relative off-diagonal stayed below `stop` as
+// converged, resets the per-sweep counters and stores the number of
+// unconverged problems in sync[2].
+template <typename T>
+__device__ inline void sweep_end(const SvdBatch& B, float stop, double* work_flops) {
+  unsigned cnt = 0;
+  for (int i = 0; i < B.n; ++i) {
+    const SvdDesc& P = B.d[i];
+    if (!*P.conv) {
+      // work of this sweep: every pair's dots, and the rotations applied
+      if (work_flops) {
+        const double pairs = 0.5 * P.n_vec * (P.n_vec - 1);
+        work_flops[0] += 16.0 * P.len * pairs + 20.0 * (P.len + P.n_vec) * (double)*P.rotated;
+        work_flops[1] += 1.0;  // sweeps, summed over the problems of the batch
+      }
+      bool done = *P.rotated == 0 || __uint_as_float(*P.maxr) < stop;
+      if constexpr (Prec<T>::tracks_norms) {
+        // the estimate behind the tail rule failed: drop the rule and
+        // sweep on until every pair is orthogonal
+        if (done && !svd_tail_rule_holds(P)) {
+          P.sig[P.n_vec + 2] = 0.0;
+          done = false;
+        }
+      }
+      if (done) *P.conv = 1;
+      else ++cnt;
+    }
+    *P.rotated = 0;
+    *P.maxr = 0u;
+  }
+  *(volatile unsigned*)(B.sync + 2) = cnt;
+  __threadfence_system();
+}
+
 // All sweeps of one phase in one cooperative launch: rounds separated by grid
 // barriers, warps striding over the pairs of all problems; after each sweep
 // block 0 marks converged problems (no rotation, or the largest relative
@@ -473,35 +534,346 @@ __global__ void __launch_bounds__(SVD_WARPS * 32) svd_sweeps(const __grid_consta
       }
       if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      unsigned cnt = 0;
-      for (int i = 0; i < B.n; ++i) {
-        const SvdDesc& P = B.d[i];
-        if (!*P.conv) {
-          // work of this sweep: every pair's dots, and the rotations applied
-          if (work_flops) {
-            const double pairs = 0.5 * P.n_vec * (P.n_vec - 1);
-            work_flops[0] += 16.0 * P.len * pairs + 20.0 * (P.len + P.n_vec) * (double)*P.rotated;
-            work_flops[1] += 1.0;  // sweeps, summed over the problems of the batch
-          }
-          bool done = *P.rotated == 0 || __uint_as_float(*P.maxr) < stop;
-          if constexpr (Prec<T>::tracks_norms) {
-            // the estimate behind the tail rule failed: drop the rule and
-            // sweep on until every pair is orthogonal
-            if (done && !svd_tail_rule_holds(P)) {
-              P.sig[P.n_vec + 2] = 0.0;
-              done = false;
-            }
-          }
-          if (done) *P.conv = 1;
-          else ++cnt;
-        }
-        *P.rotated = 0;
-        *P.maxr = 0u;
-      }
-      *unconv = cnt;
-      __threadfence_system();
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_end<T>(B, stop, work_flops);
+    if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
+    if (*unconv == 0) return;
+  }
+  if (fatal && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, 16);
+}
+
+
+// ---------------------------------------------------------------------------
+// Block Jacobi. The vectors are grouped into blocks of W and the blocks are
+// paired round-robin (nb - 1 block rounds per sweep, a grid barrier between
+// rounds). A CTA of W warps takes one pair of blocks at a time: it loads the
+// 2W vectors into shared memory and rotates them there -- in the first block
+// round of a sweep the pairs inside each block, then in every block round the
+// W^2 pairs across the two blocks, in local rounds of W disjoint pairs, a warp
+// per pair -- so each pair of vectors is visited once per sweep, as in the
+// scalar order, while each vector crosses global memory once per W of its
+// pairs. The squared norms are computed once per visit and then updated from
+// the rotations, so a pair only needs its cross product. The rotations are
+// recorded and replayed on the 2W rows of Acc afterwards, a thread per column
+// with the column in registers. Vectors of at most 512 elements.
+// ---------------------------------------------------------------------------
+template <typename T, int W>
+struct BlockCfg {
+  static constexpr int THREADS = 32 * W;  // a warp per pair of a local round
+  static constexpr int LMAX = 512;        // longest vector held in shared memory
+  static constexpr int EPT = LMAX / 32;   // elements of each vector per lane
+  static constexpr int MAX_STEPS = (W - 1) + W;
+  static_assert(W % 2 == 0 && W >= 2, "block shape");
+};
+
+template <typename T>
+struct RotRec {
+  typename Prec<T>::R cs;
+  T m1, m2;  // identity rotation: cs = 1, m1 = m2 = 0
+};
+
+template <typename T, int W>
+constexpr size_t block_smem_bytes() {
+  using C = BlockCfg<T, W>;
+  using R = typename Prec<T>::R;
+  size_t b = (size_t)2 * W * C::LMAX * sizeof(T);       // the vectors
+  b += (size_t)C::MAX_STEPS * W * sizeof(RotRec<T>);    // rotation record
+  b += (size_t)2 * W * sizeof(R);                       // squared norms
+  return b;
+}
+
+// Round-robin pairing of n_even items: pair `k` of round `r` (0 <= r < n_even - 1).
+__host__ __device__ constexpr void rr_pair(int n_even, int r, int k, int& p, int& q) {
+  p = k == 0 ? n_even - 1 : (r + k) % (n_even - 1);
+  q = k == 0 ? r : (r - k + (n_even - 1)) % (n_even - 1);
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// Rotation parameters with few FP64 operations: the angle's tangent is found
+// in FP32 from the FP64 Gram entries, the rotation built from it is unitary
+// to FP64 rounding (cs = 1/sqrt(1 + t^2), |e^{i phi}| = 1 in FP64). A tangent
+// off by the FP32 rounding leaves a relative off-diagonal of ~1e-7 of the one
+// removed, which the quadratic convergence of the sweeps absorbs. Returns
+// false when the pair needs no rotation; a2, b2 receive the new squared norms.
+template <typename T>
+__device__ inline bool jacobi_rotation_fast(const SvdDesc& P, typename Prec<T>::R a, typename Prec<T>::R b,
+                                            typename Prec<T>::R kr, typename Prec<T>::R ki, RotRec<T>& rec,
+                                            typename Prec<T>::R& a2, typename Prec<T>::R& b2, float& ratio) {
+  using R = typename Prec<T>::R;
+  const R k2 = kr * kr + ki * ki;
+  if (!(k2 > (Prec<T>::tol * Prec<T>::tol) * a * b)) return false;
+  if (a < Prec<T>::zero_level(P) || b < Prec<T>::zero_level(P)) return false;
+  const R rk = rsqrt(k2);
+  const R ak = k2 * rk;
+  ratio = (float)ak * rsqrtf((float)a) * rsqrtf((float)b);
+  const float zf = (float)((b - a) * (R(0.5) * rk));
+  // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); 1 / (2 |zeta|) where zeta^2
+  // would overflow (strongly graded pairs: tiny but necessary rotations)
+  const float az = fabsf(zf);
+  const float tf = copysignf(az > 1e18f ? 0.5f / az : 1.0f / (az + sqrtf(1.0f + az * az)), zf);
+  const R t = (R)tf;
+  const R cs = rsqrt(R(1) + t * t);
+  const R sn = cs * t;
+  const R phr = kr * rk, phi = ki * rk;
+  // x' = cs x - sn e^{-i phi} y ; y' = sn e^{i phi} x + cs y
+  rec.cs = cs;
+  rec.m1 = Prec<T>::mk(-sn * phr, sn * phi);
+  rec.m2 = Prec<T>::mk(sn * phr, sn * phi);
+  // |x'|^2 = cs^2 (a + t^2 b - 2 t |k|), |y'|^2 = cs^2 (b + t^2 a + 2 t |k|)
+  const R c2 = cs * cs;
+  a2 = c2 * (a + t * t * b - R(2) * t * ak);
+  b2 = c2 * (b + t * t * a + R(2) * t * ak);
+  return true;
+}
+
+template <typename T>
+__device__ inline void apply_rot(T& u, T& v, const RotRec<T>& r) {
+  const T x = u, y = v;
+  u = Prec<T>::mk(r.cs * x.x + r.m1.x * y.x - r.m1.y * y.y, r.cs * x.y + r.m1.x * y.y + r.m1.y * y.x);
+  v = Prec<T>::mk(r.cs * y.x + r.m2.x * x.x - r.m2.y * x.y, r.cs * y.y + r.m2.x * x.y + r.m2.y * x.x);
+}
+
+// One local round: warp w rotates local vectors (lp, lq); every thread of the
+// CTA calls it (it ends with a barrier).
+template <typename T, int W>
+__device__ inline void block_local_round(const SvdDesc& P, T* xs, typename Prec<T>::R* nrm, RotRec<T>* seq,
+                                         int slot, const int* vrows, int lp, int lq, double tau, int* n_rot,
+                                         unsigned* maxr_bits) {
+  using C = BlockCfg<T, W>;
+  using R = typename Prec<T>::R;
+  const int lane = threadIdx.x & 31;
+  const bool active = vrows[lp] >= 0 && vrows[lq] >= 0;
+  T* x = xs + lp * C::LMAX;
+  T* y = xs + lq * C::LMAX;
+  R kr = 0, ki = 0;
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < C::EPT; ++i) {
+      const T u = x[lane + 32 * i], v = y[lane + 32 * i];
+      kr += u.x * v.x + u.y * v.y;  // conj(u) v
+      ki += u.x * v.y - u.y * v.x;
     }
+  }
+  kr = Prec<T>::wsum(kr);
+  ki = Prec<T>::wsum(ki);
+  RotRec<T> rec;
+  int rot = 0;
+  if (lane == 0) {
+    rec.cs = 1;
+    rec.m1 = rec.m2 = Prec<T>::mk(0, 0);
+    if (active) {
+      const R a = nrm[lp], b = nrm[lq];
+      bool tail = false;
+      if constexpr (Prec<T>::tracks_norms) tail = tau > 0.0 && (double)a < tau * tau && (double)b < tau * tau;
+      R a2, b2;
+      float ratio = 0.f;
+      if (!tail && jacobi_rotation_fast<T>(P, a, b, kr, ki, rec, a2, b2, ratio)) {
+        rot = 1;
+        nrm[lp] = a2;
+        nrm[lq] = b2;
+        atomicAdd(n_rot, 1);
+        atomicMax(maxr_bits, __float_as_uint(ratio));
+      }
+    }
+    seq[slot] = rec;
+  }
+  rot = __shfl_sync(0xffffffffu, rot, 0);
+  if (rot) {
+    rec.cs = __shfl_sync(0xffffffffu, rec.cs, 0);
+    rec.m1.x = __shfl_sync(0xffffffffu, rec.m1.x, 0);
+    rec.m1.y = __shfl_sync(0xffffffffu, rec.m1.y, 0);
+    rec.m2.x = __shfl_sync(0xffffffffu, rec.m2.x, 0);
+    rec.m2.y = __shfl_sync(0xffffffffu, rec.m2.y, 0);
+#pragma unroll
+    for (int i = 0; i < C::EPT; ++i) {
+      T u = x[lane + 32 * i], v = y[lane + 32 * i];
+      apply_rot<T>(u, v, rec);
+      x[lane + 32 * i] = u;
+      y[lane + 32 * i] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// Replays the recorded rotations on the 2W rows of Acc (a thread per column).
+template <typename T, int W>
+__device__ inline void block_replay_acc(const SvdDesc& P, const int* vrows, const RotRec<T>* seq, bool intra,
+                                        bool cross) {
+  using C = BlockCfg<T, W>;
+  T* A = Prec<T>::Acc(P);
+  const int n = P.n_vec;
+  for (int c = threadIdx.x; c < n; c += C::THREADS) {
+    T acc[2 * W];
+#pragma unroll
+    for (int k = 0; k < 2 * W; ++k) {
+      const int r = vrows[k];
+      acc[k] = r >= 0 ? A[(int64_t)r * n + c] : Prec<T>::mk(0, 0);
+    }
+    int base = 0;
+    if (intra) {
+#pragma unroll
+      for (int rr = 0; rr < W - 1; ++rr) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          int p = 0, q = 0;
+          rr_pair(W, rr, w % (W / 2), p, q);
+          const int o = w < W / 2 ? 0 : W;
+          const RotRec<T> rec = seq[rr * W + w];
+          apply_rot<T>(acc[p + o], acc[q + o], rec);
+        }
+      }
+      base = (W - 1) * W;
+    }
+    if (cross) {
+#pragma unroll
+      for (int rr = 0; rr < W; ++rr) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const RotRec<T> rec = seq[base + rr * W + w];
+          apply_rot<T>(acc[w], acc[W + (w + rr) % W], rec);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * W; ++k) {
+      const int r = vrows[k];
+      if (r >= 0) A[(int64_t)r * n + c] = acc[k];
+    }
+  }
+}
+
+// One visit: blocks bi and bj (bj may be the padding block) of problem P.
+template <typename T, int W>
+__device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, bool use_order, T* xs,
+                            RotRec<T>* seq, typename Prec<T>::R* nrm) {
+  using C = BlockCfg<T, W>;
+  using R = typename Prec<T>::R;
+  __shared__ int vrows[2 * W];
+  __shared__ int n_rot;
+  __shared__ unsigned maxr_bits;
+  __shared__ int skip;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = P.n_vec, len = P.len;
+  const int nb = (n + W - 1) / W;
+  __syncthreads();  // the previous visit's readers of the shared state are done
+  if (tid < 2 * W) {
+    const int blk = tid < W ? bi : bj;
+    const int g = blk * W + (tid % W);
+    vrows[tid] = (blk < nb && g < n) ? (use_order ? P.perm[g] : g) : -1;
+  }
+  if (tid == 0) {
+    n_rot = 0;
+    maxr_bits = 0u;
+    skip = 0;
+  }
+  __syncthreads();
+  const bool j_real = bj < nb;
+  if (!first_round && !j_real) return;
+  double tau = 0.0;
+  if constexpr (Prec<T>::tracks_norms) {
+    tau = P.sig[n + 2];
+    if (tid == 0 && tau > 0.0) {
+      int below = 1;
+      for (int k = 0; k < 2 * W; ++k)
+        if (vrows[k] >= 0 && P.sig[vrows[k]] >= tau) below = 0;
+      skip = below;
+    }
+    __syncthreads();
+    if (skip) return;
+  }
+  T* X = Prec<T>::X(P);
+  // load the 2W vectors (zero past len and for absent vectors)
+  for (int k = 0; k < 2 * W; ++k) {
+    const int r = vrows[k];
+    for (int e = tid; e < C::LMAX; e += C::THREADS)
+      xs[k * C::LMAX + e] = (r >= 0 && e < len) ? X[(int64_t)r * len + e] : Prec<T>::mk(0, 0);
+  }
+  __syncthreads();
+  // squared norms, a warp per vector
+  for (int k = warp; k < 2 * W; k += W) {
+    R s2 = 0;
+#pragma unroll
+    for (int i = 0; i < C::EPT; ++i) {
+      const T u = xs[k * C::LMAX + lane + 32 * i];
+      s2 += u.x * u.x + u.y * u.y;
+    }
+    s2 = Prec<T>::wsum(s2);
+    if (lane == 0) nrm[k] = s2;
+  }
+  __syncthreads();
+  int step = 0;
+  if (first_round) {
+    // pairs inside each block: W - 1 rounds of W/2 pairs per block
+    for (int rr = 0; rr < W - 1; ++rr, ++step) {
+      int p, q;
+      rr_pair(W, rr, warp % (W / 2), p, q);
+      const int o = warp < W / 2 ? 0 : W;
+      block_local_round<T, W>(P, xs, nrm, seq, step * W + warp, vrows, p + o, q + o, tau, &n_rot, &maxr_bits);
+    }
+  }
+  if (j_real) {
+    for (int rr = 0; rr < W; ++rr, ++step)
+      block_local_round<T, W>(P, xs, nrm, seq, step * W + warp, vrows, warp, W + (warp + rr) % W, tau, &n_rot,
+                              &maxr_bits);
+  }
+  // vectors back to global memory; norms for the tail rule
+  for (int k = 0; k < 2 * W; ++k) {
+    const int r = vrows[k];
+    if (r < 0) continue;
+    for (int e = tid; e < len; e += C::THREADS) X[(int64_t)r * len + e] = xs[k * C::LMAX + e];
+  }
+  if constexpr (Prec<T>::tracks_norms) {
+    if (tid < 2 * W && vrows[tid] >= 0) P.sig[vrows[tid]] = sqrt(fmax((double)nrm[tid], 0.0));
+  }
+  if (tid == 0 && n_rot > 0) {
+    atomicAdd(P.rotated, n_rot);
+    atomicMax(P.maxr, maxr_bits);
+  }
+  if (n_rot > 0) block_replay_acc<T, W>(P, vrows, seq, first_round, j_real);
+}
+
+// All sweeps of one phase with the block order (see above); one CTA per SM.
+template <typename T, int W>
+__global__ void __launch_bounds__(32 * W, 1) svd_block_sweeps(const __grid_constant__ SvdBatch B, int nbpad_max,
+                                                             float stop, int max_sweeps, int fatal, int use_order,
+                                                             double* work_flops) {
+  using C = BlockCfg<T, W>;
+  using R = typename Prec<T>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);
+  RotRec<T>* seq = reinterpret_cast<RotRec<T>*>(smem_raw + (size_t)2 * W * C::LMAX * sizeof(T));
+  R* nrm = reinterpret_cast<R*>(seq + C::MAX_STEPS * W);
+  __shared__ int off[MAXB + 1];
+  if (threadIdx.x == 0) {
+    off[0] = 0;
+    for (int i = 0; i < B.n; ++i) {
+      const int nb = (B.d[i].n_vec + W - 1) / W;
+      off[i + 1] = off[i] + (nb + (nb & 1)) / 2;
+    }
+  }
+  __syncthreads();
+  const int total = off[B.n];
+  volatile unsigned* unconv = B.sync + 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int br = 0; br < nbpad_max - 1; ++br) {
+      for (int u = blockIdx.x; u < total; u += gridDim.x) {
+        int pid = 0;
+        while (u >= off[pid + 1]) ++pid;
+        const SvdDesc& P = B.d[pid];
+        if (*(volatile int*)P.conv) continue;
+        const int nb = (P.n_vec + W - 1) / W;
+        const int nbp = nb + (nb & 1);
+        if (br >= nbp - 1) continue;
+        int bi, bj;
+        rr_pair(nbp, br, u - off[pid], bi, bj);
+        block_visit<T, W>(P, bi, bj, br == 0, use_order != 0, xs, seq, nrm);
+      }
+      if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_end<T>(B, stop, work_flops);
     if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
     if (*unconv == 0) return;
   }
@@ -671,6 +1043,42 @@ static void jacobi_sweeps(SvdBatch& b, int npad_max, float stop, int fatal, cuda
   ++g_launches;
 }
 
+// block sweeps (vectors of at most 512 elements); false if they cannot run
+template <typename T, int W>
+static bool block_sweeps(SvdBatch& b, float stop, int fatal, int use_order, cudaStream_t s, const char* name) {
+  using C = BlockCfg<T, W>;
+  static int max_blocks = -1;
+  const size_t smem = block_smem_bytes<T, W>();
+  if (max_blocks < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaFuncSetAttribute(svd_block_sweeps<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_block_sweeps<T, W>, C::THREADS, smem));
+    max_blocks = sms * std::min(per_sm, 1);
+  }
+  if (max_blocks <= 0) return false;
+  int total = 0, nbpad_max = 2;
+  for (int i = 0; i < b.n; ++i) {
+    if (b.d[i].len > C::LMAX) return false;
+    const int nb = cdiv(b.d[i].n_vec, W);
+    total += (nb + (nb & 1)) / 2;
+    nbpad_max = std::max(nbpad_max, nb + (nb & 1));
+  }
+  const int blocks = std::max(1, std::min(max_blocks, total));
+  CUDA_TRY(cudaMemsetAsync(b.sync, 0, 4 * sizeof(unsigned), s));
+  int max_sweeps = SVD_MAX_SWEEPS;
+  double* work_dev = nullptr;
+  const double* work_host = prof_work_slot(&work_dev);
+  void* args[] = {(void*)&b,     (void*)&nbpad_max, (void*)&stop,    (void*)&max_sweeps,
+                  (void*)&fatal, (void*)&use_order, (void*)&work_dev};
+  ProfScope ps(name, s, 0.0, 0.0, work_host);
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)svd_block_sweeps<T, W>, dim3(blocks), dim3(C::THREADS), args,
+                                       smem, s));
+  ++g_launches;
+  return true;
+}
+
 void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   if (b.n <= 0) return;
   int64_t max_elems = 1;
@@ -694,7 +1102,8 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   // FP32 phase: until the largest relative off-diagonal of a sweep is < 1e-4
   // (just above the FP32 rounding of the dot products); not converging here
   // only means a weaker preconditioner
-  jacobi_sweeps<float2>(b, npad_max, 1e-4f, 0, s, "svd_jacobi_fp32");
+  if (!block_sweeps<float2, 16>(b, 1e-4f, 0, 0, s, "svd_jacobi_fp32"))
+    jacobi_sweeps<float2>(b, npad_max, 1e-4f, 0, s, "svd_jacobi_fp32");
   // ---- phase 2: unitary FP64 rotation and FP64 vectors ----
   svd_acc_to64<<<g1, 256, 0, s>>>(b);
   LAUNCH_CHECK();
@@ -740,13 +1149,15 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   dim3 gn(cdiv(nvec_max, SVD_WARPS), b.n);
   svd_norms<<<gn, SVD_WARPS * 32, 0, s>>>(b);
   LAUNCH_CHECK();
-  const size_t tail_smem = nvec_max <= SVD_TAIL_MAX ? (size_t)nvec_max * sizeof(double) : 0;
+  const size_t tail_smem = (size_t)std::min(nvec_max, SVD_TAIL_MAX) * sizeof(double);
   svd_tail_threshold<<<b.n, 256, tail_smem, s>>>(b);
   LAUNCH_CHECK();
   g_launches += 2;
   // stop after a sweep whose largest relative off-diagonal was below 1e-7 (full:
   // ~1e-14 left) or 1e-4 (mixed-precision sweeps: ~1e-8 or less left)
-  jacobi_sweeps<double2>(b, npad_max, b.mode == 0 ? 1e-7f : 1e-4f, 1, s, "svd_jacobi_fp64");
+  const float stop64 = b.mode == 0 ? 1e-7f : 1e-4f;
+  if (!block_sweeps<double2, 8>(b, stop64, 1, 1, s, "svd_jacobi_fp64"))
+    jacobi_sweeps<double2>(b, npad_max, stop64, 1, s, "svd_jacobi_fp64");
   svd_norms<<<gn, SVD_WARPS * 32, 0, s>>>(b);
   LAUNCH_CHECK();
   svd_truncate<<<b.n, 256, 0, s>>>(b);
