@@ -49,7 +49,35 @@ def parse():
     ap.add_argument("--chi", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--svd-case", type=int, default=0,
+                    help="profiling case: two truncated splits of one N x N two-site state "
+                         "(half the spectrum kept), no benchmark line")
     return ap.parse_args()
+
+
+def svd_case(n):
+    """The split of one evolved two-site state (Fig. 5) at chi = n / 2: a seeded
+    n x n matrix whose singular values fall from 1 to 6.5e-3 over the first
+    half (the previous bond's Schmidt values) and from 7e-4 to 4e-6 over the
+    second (the weight one time step moves into new directions), truncated to
+    n / 2 values, run twice through tdvp_op_split. A small, self-contained case
+    for kernel profiles of the Jacobi sweeps."""
+    import torch
+    from paper_1912_06127_gb300 import tdvp
+    U = np.linalg.qr(I.random_complex((n, n), 5))[0]
+    Vh = np.linalg.qr(I.random_complex((n, n), 6))[0]
+    s = np.concatenate([np.geomspace(1.0, 6.5e-3, n // 2), np.geomspace(7e-4, 4e-6, n - n // 2)])
+    th = torch.from_numpy(((U * s) @ Vh).reshape(-1).view(np.float64).copy()).cuda()
+    for _ in range(2):
+        PsiL = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+        PsiR = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+        V = torch.zeros(n, dtype=torch.float64, device="cuda")
+        chi, w = tdvp.op_split(n, n, th, n // 2, 0.0, 1e-12, PsiL, V, PsiR, None)
+        torch.cuda.synchronize()
+    w_ref = float((s[n // 2:] ** 2).sum())
+    print(json.dumps({"svd_case": n, "chi": chi, "w": w, "w_expected": w_ref}))
+    if chi != n // 2 or abs(w - w_ref) > 1e-9 * w_ref:
+        raise SystemExit("svd case: unexpected truncation")
 
 
 def workload(args):
@@ -377,6 +405,9 @@ def state_gb(mdl, chi):
 
 def main():
     args = parse()
+    if args.svd_case:
+        svd_case(args.svd_case)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

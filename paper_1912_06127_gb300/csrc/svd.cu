@@ -599,13 +599,13 @@ __host__ __device__ constexpr void rr_pair(int n_even, int r, int k, int& p, int
 // removed, which the quadratic convergence of the sweeps absorbs. Returns
 // false when the pair needs no rotation; a2, b2 receive the new squared norms.
 template <typename T>
-__device__ inline bool jacobi_rotation_fast(const SvdDesc& P, typename Prec<T>::R a, typename Prec<T>::R b,
+__device__ inline bool jacobi_rotation_fast(typename Prec<T>::R zl, typename Prec<T>::R a, typename Prec<T>::R b,
                                             typename Prec<T>::R kr, typename Prec<T>::R ki, RotRec<T>& rec,
                                             typename Prec<T>::R& a2, typename Prec<T>::R& b2, float& ratio) {
   using R = typename Prec<T>::R;
   const R k2 = kr * kr + ki * ki;
   if (!(k2 > (Prec<T>::tol * Prec<T>::tol) * a * b)) return false;
-  if (a < Prec<T>::zero_level(P) || b < Prec<T>::zero_level(P)) return false;
+  if (a < zl || b < zl) return false;  // zl: Prec<T>::zero_level
   const R rk = rsqrt(k2);
   const R ak = k2 * rk;
   ratio = (float)ak * rsqrtf((float)a) * rsqrtf((float)b);
@@ -639,7 +639,7 @@ __device__ inline void apply_rot(T& u, T& v, const RotRec<T>& r) {
 // One local round: warp w rotates local vectors (lp, lq); every thread of the
 // CTA calls it (it ends with a barrier).
 template <typename T, int W>
-__device__ inline void block_local_round(const SvdDesc& P, T* xs, typename Prec<T>::R* nrm, RotRec<T>* seq,
+__device__ inline void block_local_round(typename Prec<T>::R zl, T* xs, typename Prec<T>::R* nrm, RotRec<T>* seq,
                                          int slot, const int* vrows, int lp, int lq, double tau, int* n_rot,
                                          unsigned* maxr_bits) {
   using C = BlockCfg<T, W>;
@@ -670,7 +670,7 @@ __device__ inline void block_local_round(const SvdDesc& P, T* xs, typename Prec<
       if constexpr (Prec<T>::tracks_norms) tail = tau > 0.0 && (double)a < tau * tau && (double)b < tau * tau;
       R a2, b2;
       float ratio = 0.f;
-      if (!tail && jacobi_rotation_fast<T>(P, a, b, kr, ki, rec, a2, b2, ratio)) {
+      if (!tail && jacobi_rotation_fast<T>(zl, a, b, kr, ki, rec, a2, b2, ratio)) {
         rot = 1;
         nrm[lp] = a2;
         nrm[lq] = b2;
@@ -747,8 +747,8 @@ __device__ inline void block_replay_acc(const SvdDesc& P, const int* vrows, cons
 
 // One visit: blocks bi and bj (bj may be the padding block) of problem P.
 template <typename T, int W>
-__device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, bool use_order, T* xs,
-                            RotRec<T>* seq, typename Prec<T>::R* nrm) {
+__device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, bool use_order, bool skip_acc,
+                            T* xs, RotRec<T>* seq, typename Prec<T>::R* nrm) {
   using C = BlockCfg<T, W>;
   using R = typename Prec<T>::R;
   __shared__ int vrows[2 * W];
@@ -804,6 +804,7 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
     if (lane == 0) nrm[k] = s2;
   }
   __syncthreads();
+  const R zl = Prec<T>::zero_level(P);
   int step = 0;
   if (first_round) {
     // pairs inside each block: W - 1 rounds of W/2 pairs per block
@@ -811,12 +812,12 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
       int p, q;
       rr_pair(W, rr, warp % (W / 2), p, q);
       const int o = warp < W / 2 ? 0 : W;
-      block_local_round<T, W>(P, xs, nrm, seq, step * W + warp, vrows, p + o, q + o, tau, &n_rot, &maxr_bits);
+      block_local_round<T, W>(zl, xs, nrm, seq, step * W + warp, vrows, p + o, q + o, tau, &n_rot, &maxr_bits);
     }
   }
   if (j_real) {
     for (int rr = 0; rr < W; ++rr, ++step)
-      block_local_round<T, W>(P, xs, nrm, seq, step * W + warp, vrows, warp, W + (warp + rr) % W, tau, &n_rot,
+      block_local_round<T, W>(zl, xs, nrm, seq, step * W + warp, vrows, warp, W + (warp + rr) % W, tau, &n_rot,
                               &maxr_bits);
   }
   // vectors back to global memory; norms for the tail rule
@@ -832,14 +833,14 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
     atomicAdd(P.rotated, n_rot);
     atomicMax(P.maxr, maxr_bits);
   }
-  if (n_rot > 0) block_replay_acc<T, W>(P, vrows, seq, first_round, j_real);
+  if (n_rot > 0 && !skip_acc) block_replay_acc<T, W>(P, vrows, seq, first_round, j_real);
 }
 
 // All sweeps of one phase with the block order (see above); one CTA per SM.
 template <typename T, int W>
 __global__ void __launch_bounds__(32 * W, 1) svd_block_sweeps(const __grid_constant__ SvdBatch B, int nbpad_max,
                                                              float stop, int max_sweeps, int fatal, int use_order,
-                                                             double* work_flops) {
+                                                             int skip_acc, double* work_flops) {
   using C = BlockCfg<T, W>;
   using R = typename Prec<T>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -869,7 +870,7 @@ __global__ void __launch_bounds__(32 * W, 1) svd_block_sweeps(const __grid_const
         if (br >= nbp - 1) continue;
         int bi, bj;
         rr_pair(nbp, br, u - off[pid], bi, bj);
-        block_visit<T, W>(P, bi, bj, br == 0, use_order != 0, xs, seq, nrm);
+        block_visit<T, W>(P, bi, bj, br == 0, use_order != 0, skip_acc != 0, xs, seq, nrm);
       }
       if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
     }
@@ -987,6 +988,23 @@ __global__ void svd_truncate(const __grid_constant__ SvdBatch B) {
   *P.w = tail;
 }
 
+// Mode 1: the kept vectors in descending order, each divided by its norm
+// (rows of V^H), as the operand of the GEMM with theta; zero past chi.
+__global__ void svd_gather_kept(const __grid_constant__ SvdBatch B) {
+  const SvdDesc& P = B.d[blockIdx.y];
+  const int chi = *P.chi;
+  const int64_t n = (int64_t)P.kcap * P.len;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / P.len), e = (int)(idx % P.len);
+    double2 v = make_double2(0.0, 0.0);
+    if (c < chi) {
+      const int i = P.perm[c];
+      v = zscale(P.X[(int64_t)i * P.len + e], 1.0 / P.sig[i]);
+    }
+    P.P[idx] = v;
+  }
+}
+
 __global__ void svd_write(const __grid_constant__ SvdBatch B) {
   const SvdDesc& P = B.d[blockIdx.y];
   const int chi = *P.chi;
@@ -998,8 +1016,9 @@ __global__ void svd_write(const __grid_constant__ SvdBatch B) {
       const int r = (int)(idx / chi), c = (int)(idx % chi);
       const int i = P.perm[c];
       double2 v;
-      if (!P.trans) v = zscale(zconj(P.Acc[(int64_t)i * P.n_vec + r]), P.sig[i]);
-      else v = P.X[(int64_t)i * P.len + r];
+      if (P.trans) v = P.X[(int64_t)i * P.len + r];
+      else if (B.mode == 1) v = P.T[(int64_t)r * P.kcap + c];
+      else v = zscale(zconj(P.Acc[(int64_t)i * P.n_vec + r]), P.sig[i]);
       P.PsiL[idx] = v;
     } else if (idx < nl + nr) {
       const int64_t q = idx - nl;
@@ -1007,6 +1026,7 @@ __global__ void svd_write(const __grid_constant__ SvdBatch B) {
       const int i = P.perm[c];
       double2 v;
       if (!P.trans) v = P.X[(int64_t)i * P.len + col];
+      else if (B.mode == 1) v = P.T[(int64_t)c * P.cols + col];
       else v = zscale(zconj(P.Acc[(int64_t)i * P.n_vec + col]), P.sig[i]);
       P.PsiR[q] = v;
     } else {
@@ -1045,7 +1065,8 @@ static void jacobi_sweeps(SvdBatch& b, int npad_max, float stop, int fatal, cuda
 
 // block sweeps (vectors of at most 512 elements); false if they cannot run
 template <typename T, int W>
-static bool block_sweeps(SvdBatch& b, float stop, int fatal, int use_order, cudaStream_t s, const char* name) {
+static bool block_sweeps(SvdBatch& b, float stop, int fatal, int use_order, int skip_acc, cudaStream_t s,
+                         const char* name) {
   using C = BlockCfg<T, W>;
   static int max_blocks = -1;
   const size_t smem = block_smem_bytes<T, W>();
@@ -1070,8 +1091,8 @@ static bool block_sweeps(SvdBatch& b, float stop, int fatal, int use_order, cuda
   int max_sweeps = SVD_MAX_SWEEPS;
   double* work_dev = nullptr;
   const double* work_host = prof_work_slot(&work_dev);
-  void* args[] = {(void*)&b,     (void*)&nbpad_max, (void*)&stop,    (void*)&max_sweeps,
-                  (void*)&fatal, (void*)&use_order, (void*)&work_dev};
+  void* args[] = {(void*)&b,         (void*)&nbpad_max, (void*)&stop,     (void*)&max_sweeps,
+                  (void*)&fatal,     (void*)&use_order, (void*)&skip_acc, (void*)&work_dev};
   ProfScope ps(name, s, 0.0, 0.0, work_host);
   CUDA_TRY(cudaLaunchCooperativeKernel((const void*)svd_block_sweeps<T, W>, dim3(blocks), dim3(C::THREADS), args,
                                        smem, s));
@@ -1102,7 +1123,7 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   // FP32 phase: until the largest relative off-diagonal of a sweep is < 1e-4
   // (just above the FP32 rounding of the dot products); not converging here
   // only means a weaker preconditioner
-  if (!block_sweeps<float2, 16>(b, 1e-4f, 0, 0, s, "svd_jacobi_fp32"))
+  if (!block_sweeps<float2, 16>(b, 1e-4f, 0, 0, 0, s, "svd_jacobi_fp32"))
     jacobi_sweeps<float2>(b, npad_max, 1e-4f, 0, s, "svd_jacobi_fp32");
   // ---- phase 2: unitary FP64 rotation and FP64 vectors ----
   svd_acc_to64<<<g1, 256, 0, s>>>(b);
@@ -1156,12 +1177,42 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   // stop after a sweep whose largest relative off-diagonal was below 1e-7 (full:
   // ~1e-14 left) or 1e-4 (mixed-precision sweeps: ~1e-8 or less left)
   const float stop64 = b.mode == 0 ? 1e-7f : 1e-4f;
-  if (!block_sweeps<double2, 8>(b, stop64, 1, 1, s, "svd_jacobi_fp64"))
+  if (!block_sweeps<double2, 8>(b, stop64, 1, 1, b.mode == 1 ? 1 : 0, s, "svd_jacobi_fp64"))
     jacobi_sweeps<double2>(b, npad_max, stop64, 1, s, "svd_jacobi_fp64");
   svd_norms<<<gn, SVD_WARPS * 32, 0, s>>>(b);
   LAUNCH_CHECK();
   svd_truncate<<<b.n, 256, 0, s>>>(b);
   LAUNCH_CHECK();
+  if (b.mode == 1) {
+    // the other factor of the kept triplets from theta: U Lambda = theta V
+    // (vectors = rows) or Lambda V^H = U^H theta (vectors = columns)
+    int64_t kl_max = 1;
+    ZGemmBatch go{};
+    go.n = b.n;
+    for (int i = 0; i < b.n; ++i) {
+      SvdDesc& P = b.d[i];
+      P.kcap = std::min(P.chi_max, P.n_vec);
+      kl_max = std::max<int64_t>(kl_max, (int64_t)P.kcap * P.len);
+      ZGemmDesc& g = go.d[i];
+      g = ZGemmDesc{};
+      if (!P.trans) {  // C[r][c] = sum_e theta[r][e] conj(Xs[c][e])
+        g.M = P.rows; g.N = P.kcap; g.K = P.len;
+        g.A = P.theta; g.a_rs = P.cols; g.a_cs = 1;
+        g.B = P.P; g.b_rs = 1; g.b_cs = P.len; g.conj_b = 1;
+        g.C = P.T; g.c_rs = P.kcap; g.c_cs = 1;
+      } else {         // C[c][col] = sum_e conj(Xs[c][e]) theta[e][col]
+        g.M = P.kcap; g.N = P.cols; g.K = P.len;
+        g.A = P.P; g.a_rs = P.len; g.a_cs = 1; g.conj_a = 1;
+        g.B = P.theta; g.b_rs = P.cols; g.b_cs = 1;
+        g.C = P.T; g.c_rs = P.cols; g.c_cs = 1;
+      }
+    }
+    dim3 gg((unsigned)std::min<int64_t>(cdiv64(kl_max, 256), 152 * 8), b.n);
+    svd_gather_kept<<<gg, 256, 0, s>>>(b);
+    LAUNCH_CHECK();
+    ++g_launches;
+    launch_zgemm(go, s, "svd_vectors_zgemm");
+  }
   dim3 gw((unsigned)std::min<int64_t>(cdiv64(max_elems, 256), 152 * 8), b.n);
   svd_write<<<gw, 256, 0, s>>>(b);
   LAUNCH_CHECK();
