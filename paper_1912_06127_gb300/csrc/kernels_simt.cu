@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const __grid_constant__ ZGem
   const int tiles_n = (P.N + ZG_BN - 1) / ZG_BN;
   if ((int)blockIdx.x >= tiles_m * tiles_n) return;
   const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  if (P.upper_only && tm > tn) return;
   const int m0 = tm * ZG_BM, n0 = tn * ZG_BN;
   __shared__ double2 As[ZG_BK][ZG_BM];
   __shared__ double2 Bs[ZG_BK][ZG_BN];
@@ -119,7 +120,7 @@ void launch_zgemm(const ZGemmBatch& b, cudaStream_t s, const char* prof_name) {
   double fl = 0, by = 0;
   for (int i = 0; i < b.n; ++i) {
     const auto& d = b.d[i];
-    fl += 8.0 * d.M * d.N * d.K;
+    fl += (d.upper_only ? 4.0 : 8.0) * d.M * d.N * d.K;
     by += 16.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
   }
   ProfScope ps(prof_name, s, fl, by);

@@ -896,13 +896,94 @@ __global__ void svd_acc_to64(const __grid_constant__ SvdBatch B) {
   }
 }
 
-// Newton-Schulz step for the unitary polar factor: Acc <- 1.5 Acc - 0.5 T, T = Acc Acc^H Acc
+// Newton-Schulz step for the unitary polar factor, Acc <- 1.5 Acc - 0.5 Acc Acc^H Acc,
+// written as Acc <- Acc + 0.5 E Acc with E = I - Acc Acc^H. E is small (the
+// unitarity defect), so E Acc only needs FP32: its rounding, ~6e-8 |E|, stays
+// below the FP64 rounding of Acc once |E| < 1e-8. P = Acc Acc^H (FP64, upper
+// tiles only: Hermitian) comes from the FP64 GEMM; this kernel forms E from it
+// and writes T = E Acc (64 x 64 output tiles, 4 x 4 per thread).
+constexpr int NS_T = 64, NS_BK = 8;
+__global__ void __launch_bounds__(256) svd_ns_correction(const __grid_constant__ SvdBatch B) {
+  const SvdDesc& P = B.d[blockIdx.y];
+  const int n = P.n_vec;
+  const int tiles = (n + NS_T - 1) / NS_T;
+  if ((int)blockIdx.x >= tiles * tiles) return;
+  const int m0 = (blockIdx.x % tiles) * NS_T, n0 = (blockIdx.x / tiles) * NS_T;
+  __shared__ float2 As[NS_BK][NS_T];
+  __shared__ float2 Bs[NS_BK][NS_T];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < n; k0 += NS_BK) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int e = tid + r * 256;
+      {  // E(i, k) = delta_ik - P(i, k); P(i, k) = conj(P(k, i)) below the diagonal tiles
+        const int k = e % NS_BK, i = e / NS_BK;
+        const int gi = m0 + i, gk = k0 + k;
+        float2 v = make_float2(0.f, 0.f);
+        if (gi < n && gk < n) {
+          double2 p;
+          if (gi / NS_T <= gk / NS_T) {
+            p = P.P[(int64_t)gi * n + gk];
+          } else {
+            p = P.P[(int64_t)gk * n + gi];
+            p.y = -p.y;
+          }
+          v = make_float2((float)((gi == gk ? 1.0 : 0.0) - p.x), (float)(-p.y));
+        }
+        As[k][i] = v;
+      }
+      {
+        const int j = e % NS_T, k = e / NS_T;
+        const int gj = n0 + j, gk = k0 + k;
+        float2 w = make_float2(0.f, 0.f);
+        if (gj < n && gk < n) {
+          const double2 a = P.Acc[(int64_t)gk * n + gj];
+          w = make_float2((float)a.x, (float)a.y);
+        }
+        Bs[k][j] = w;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < NS_BK; ++kk) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = m0 + ty + 16 * i;
+    if (gi >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = n0 + tx + 16 * j;
+      if (gj < n) P.T[(int64_t)gi * n + gj] = make_double2(acc[i][j].x, acc[i][j].y);
+    }
+  }
+}
+
 __global__ void svd_ns_combine(const __grid_constant__ SvdBatch B) {
   const SvdDesc& P = B.d[blockIdx.y];
   const int64_t na = (int64_t)P.n_vec * P.n_vec;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += (int64_t)gridDim.x * blockDim.x) {
-    double2 a = P.Acc[i], t = P.T[i];
-    P.Acc[i] = make_double2(1.5 * a.x - 0.5 * t.x, 1.5 * a.y - 0.5 * t.y);
+    const double2 a = P.Acc[i], t = P.T[i];
+    P.Acc[i] = make_double2(a.x + 0.5 * t.x, a.y + 0.5 * t.y);
   }
 }
 
@@ -1128,23 +1209,18 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   // ---- phase 2: unitary FP64 rotation and FP64 vectors ----
   svd_acc_to64<<<g1, 256, 0, s>>>(b);
   LAUNCH_CHECK();
-  ZGemmBatch gp{}, gt{}, gx{};
-  gp.n = gt.n = gx.n = b.n;
+  ZGemmBatch gp{}, gx{};
+  gp.n = gx.n = b.n;
   for (int i = 0; i < b.n; ++i) {
     const SvdDesc& P = b.d[i];
     const int n = P.n_vec;
-    ZGemmDesc& a = gp.d[i];   // P = Acc Acc^H
+    ZGemmDesc& a = gp.d[i];   // P = Acc Acc^H (Hermitian: upper tiles)
     a = ZGemmDesc{};
     a.M = a.N = a.K = n;
     a.A = P.Acc; a.a_rs = n; a.a_cs = 1;
     a.B = P.Acc; a.b_rs = 1; a.b_cs = n; a.conj_b = 1;
     a.C = P.P; a.c_rs = n; a.c_cs = 1;
-    ZGemmDesc& t = gt.d[i];   // T = P Acc
-    t = ZGemmDesc{};
-    t.M = t.N = t.K = n;
-    t.A = P.P; t.a_rs = n; t.a_cs = 1;
-    t.B = P.Acc; t.b_rs = n; t.b_cs = 1;
-    t.C = P.T; t.c_rs = n; t.c_cs = 1;
+    a.upper_only = 1;
     ZGemmDesc& x = gx.d[i];   // X = Acc . vectors(theta)
     x = ZGemmDesc{};
     x.M = n; x.N = P.len; x.K = n;
@@ -1158,11 +1234,18 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   const int ns_steps = b.mode == 0 ? 2 : 1;
   for (int it = 0; it < ns_steps; ++it) {
     launch_zgemm(gp, s, "svd_newton_schulz");
-    launch_zgemm(gt, s, "svd_newton_schulz");
+    const int nt = cdiv(nvec_max, NS_T);
+    {
+      double fl = 0.0;
+      for (int i = 0; i < b.n; ++i) fl += 8.0 * (double)b.d[i].n_vec * b.d[i].n_vec * b.d[i].n_vec;
+      ProfScope ps("svd_ns_correction_fp32", s, fl, 0.0);
+      svd_ns_correction<<<dim3(nt * nt, b.n), 256, 0, s>>>(b);
+      LAUNCH_CHECK();
+    }
     dim3 gn((unsigned)std::min<int64_t>(cdiv64((int64_t)nvec_max * nvec_max, 256), 152 * 8), b.n);
     svd_ns_combine<<<gn, 256, 0, s>>>(b);
     LAUNCH_CHECK();
-    ++g_launches;
+    g_launches += 2;
   }
   launch_zgemm(gx, s, "svd_newton_schulz");
   g_launches += 2;
