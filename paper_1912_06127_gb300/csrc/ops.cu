@@ -134,7 +134,7 @@ void Slot::ensure(int64_t vec, int64_t T, int64_t fsz, int64_t svd_n, int kmax_)
   svdX32 = dalloc<float2>(cap_vec);
   svdAcc32 = dalloc<float2>(cap_vec);
   maxr = reinterpret_cast<unsigned*>(dalloc<int>(1));
-  sync = reinterpret_cast<unsigned*>(dalloc<int>(4));
+  sync = reinterpret_cast<unsigned*>(dalloc<int>(8));
   sig = dalloc<double>(nsvd + 3);
   perm = dalloc<int>(nsvd + 1);
   rot = dalloc<int>(1);

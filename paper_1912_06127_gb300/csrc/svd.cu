@@ -324,7 +324,8 @@ __device__ inline void jacobi_pair(const SvdDesc& P, int r, int pair, int lane) 
 // Grid-wide barrier for a cooperative launch, with a bounded wait: returns
 // false (and sets the status bit and the abort word, which makes every later
 // barrier return at once) if the other blocks did not arrive in time.
-// sync[0] = arrivals, sync[1] = generation, sync[3] = abort.
+// sync[0] = arrivals, sync[1] = generation, sync[3] = abort (sync[2]: unconverged
+// problems, sync[4..5]: visit counters of the block sweeps).
 __device__ inline bool grid_barrier(unsigned* sync, unsigned nblocks, int* status) {
   __shared__ int ok_sh;
   __syncthreads();
@@ -569,6 +570,9 @@ template <typename T>
 struct RotRec {
   typename Prec<T>::R cs;
   T m1, m2;  // identity rotation: cs = 1, m1 = m2 = 0
+  // FP32 copies for the accumulation of the block rotation in FP32 (cm1 = cs - 1)
+  float cm1;
+  float2 m1f, m2f;
 };
 
 template <typename T, int W>
@@ -599,13 +603,14 @@ __host__ __device__ constexpr void rr_pair(int n_even, int r, int k, int& p, int
 // removed, which the quadratic convergence of the sweeps absorbs. Returns
 // false when the pair needs no rotation; a2, b2 receive the new squared norms.
 template <typename T>
-__device__ inline bool jacobi_rotation_fast(typename Prec<T>::R zl, typename Prec<T>::R a, typename Prec<T>::R b,
+__device__ inline bool jacobi_rotation_fast(typename Prec<T>::R tol2, typename Prec<T>::R zl, typename Prec<T>::R a,
+                                            typename Prec<T>::R b,
                                             typename Prec<T>::R kr, typename Prec<T>::R ki, RotRec<T>& rec,
                                             typename Prec<T>::R& a2, typename Prec<T>::R& b2, float& ratio) {
   using R = typename Prec<T>::R;
   const R k2 = kr * kr + ki * ki;
-  if (!(k2 > (Prec<T>::tol * Prec<T>::tol) * a * b)) return false;
-  if (a < zl || b < zl) return false;  // zl: Prec<T>::zero_level
+  if (!(k2 > tol2 * a * b)) return false;  // tol2: squared relative tolerance
+  if (a < zl || b < zl) return false;      // zl: Prec<T>::zero_level
   const R rk = rsqrt(k2);
   const R ak = k2 * rk;
   ratio = (float)ak * rsqrtf((float)a) * rsqrtf((float)b);
@@ -639,7 +644,7 @@ __device__ inline void apply_rot(T& u, T& v, const RotRec<T>& r) {
 // One local round: warp w rotates local vectors (lp, lq); every thread of the
 // CTA calls it (it ends with a barrier).
 template <typename T, int W>
-__device__ inline void block_local_round(typename Prec<T>::R zl, T* xs, typename Prec<T>::R* nrm, RotRec<T>* seq,
+__device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec<T>::R zl, T* xs, typename Prec<T>::R* nrm, RotRec<T>* seq,
                                          int slot, const int* vrows, int lp, int lq, double tau, int* n_rot,
                                          unsigned* maxr_bits) {
   using C = BlockCfg<T, W>;
@@ -664,14 +669,19 @@ __device__ inline void block_local_round(typename Prec<T>::R zl, T* xs, typename
   if (lane == 0) {
     rec.cs = 1;
     rec.m1 = rec.m2 = Prec<T>::mk(0, 0);
+    rec.cm1 = 0.f;
+    rec.m1f = rec.m2f = make_float2(0.f, 0.f);
     if (active) {
       const R a = nrm[lp], b = nrm[lq];
       bool tail = false;
       if constexpr (Prec<T>::tracks_norms) tail = tau > 0.0 && (double)a < tau * tau && (double)b < tau * tau;
       R a2, b2;
       float ratio = 0.f;
-      if (!tail && jacobi_rotation_fast<T>(zl, a, b, kr, ki, rec, a2, b2, ratio)) {
+      if (!tail && jacobi_rotation_fast<T>(tol2, zl, a, b, kr, ki, rec, a2, b2, ratio)) {
         rot = 1;
+        rec.cm1 = (float)(rec.cs - R(1));
+        rec.m1f = make_float2((float)rec.m1.x, (float)rec.m1.y);
+        rec.m2f = make_float2((float)rec.m2.x, (float)rec.m2.y);
         nrm[lp] = a2;
         nrm[lq] = b2;
         atomicAdd(n_rot, 1);
@@ -745,10 +755,103 @@ __device__ inline void block_replay_acc(const SvdDesc& P, const int* vrows, cons
   }
 }
 
-// One visit: blocks bi and bj (bj may be the padding block) of problem P.
+// The visit's rotations as one 2W x 2W matrix G = I + D, D accumulated in FP32
+// (a thread per column of D, lanes 0 .. 2W-1 of warp 0), then
+// Acc rows <- Acc rows + D Acc rows with D Acc in FP32. The rotations of the
+// FP64 sweeps are small (the FP32 phase has done the large ones), so D's
+// FP32 rounding stays ~1e-9 and Acc keeps the accuracy of the mixed mode at a
+// small fraction of the FP64 work of replaying every rotation.
 template <typename T, int W>
-__device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, bool use_order, bool skip_acc,
-                            T* xs, RotRec<T>* seq, typename Prec<T>::R* nrm) {
+__device__ inline void block_correct_acc(const SvdDesc& P, const int* vrows, const RotRec<T>* seq, bool intra,
+                                         bool cross, float2* D) {
+  using C = BlockCfg<T, W>;
+  constexpr int N2 = 2 * W;
+  const int tid = threadIdx.x;
+  if (tid < N2) {
+    const int j = tid;
+    float2 col[N2];
+#pragma unroll
+    for (int k = 0; k < N2; ++k) col[k] = make_float2(0.f, 0.f);
+    auto rot = [&](float2& u, float2& v, int p, int q, const RotRec<T>& r) {
+      // rows p, q of I + D: (e_p + D_p, e_q + D_q) -> rotated, identity parts kept exact
+      const float cs = 1.0f + r.cm1;
+      const float2 a = u, b = v;
+      float2 nu = make_float2(cs * a.x + r.m1f.x * b.x - r.m1f.y * b.y, cs * a.y + r.m1f.x * b.y + r.m1f.y * b.x);
+      float2 nv = make_float2(cs * b.x + r.m2f.x * a.x - r.m2f.y * a.y, cs * b.y + r.m2f.x * a.y + r.m2f.y * a.x);
+      if (j == p) {
+        nu.x += r.cm1;
+        nv.x += r.m2f.x;
+        nv.y += r.m2f.y;
+      }
+      if (j == q) {
+        nv.x += r.cm1;
+        nu.x += r.m1f.x;
+        nu.y += r.m1f.y;
+      }
+      u = nu;
+      v = nv;
+    };
+    int base = 0;
+    if (intra) {
+#pragma unroll
+      for (int rr = 0; rr < W - 1; ++rr) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          int p = 0, q = 0;
+          rr_pair(W, rr, w % (W / 2), p, q);
+          const int o = w < W / 2 ? 0 : W;
+          rot(col[p + o], col[q + o], p + o, q + o, seq[rr * W + w]);
+        }
+      }
+      base = (W - 1) * W;
+    }
+    if (cross) {
+#pragma unroll
+      for (int rr = 0; rr < W; ++rr) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) rot(col[w], col[W + (w + rr) % W], w, W + (w + rr) % W, seq[base + rr * W + w]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < N2; ++k) D[k * N2 + j] = col[k];
+  }
+  __syncthreads();
+  T* A = Prec<T>::Acc(P);
+  const int n = P.n_vec;
+  for (int c = tid; c < n; c += C::THREADS) {
+    float2 af[N2];
+#pragma unroll
+    for (int k = 0; k < N2; ++k) {
+      const int r = vrows[k];
+      const T a = r >= 0 ? A[(int64_t)r * n + c] : Prec<T>::mk(0, 0);
+      af[k] = make_float2((float)a.x, (float)a.y);
+    }
+#pragma unroll
+    for (int k = 0; k < N2; ++k) {
+      const int r = vrows[k];
+      if (r < 0) continue;
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int jj = 0; jj < N2; ++jj) {
+        const float2 d = D[k * N2 + jj];
+        s.x = fmaf(d.x, af[jj].x, fmaf(-d.y, af[jj].y, s.x));
+        s.y = fmaf(d.x, af[jj].y, fmaf(d.y, af[jj].x, s.y));
+      }
+      T a = A[(int64_t)r * n + c];
+      a.x += s.x;
+      a.y += s.y;
+      A[(int64_t)r * n + c] = a;
+    }
+  }
+}
+
+// One visit: blocks bi and bj (bj may be the padding block) of problem P.
+// acc_mode 0: replay every rotation on Acc; 1: block_correct_acc (FP64 sweeps
+// of the mixed mode).
+
+template <typename T, int W>
+__device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, bool use_order, int acc_mode,
+                            typename Prec<T>::R tol, T* xs, RotRec<T>* seq, typename Prec<T>::R* nrm) {
   using C = BlockCfg<T, W>;
   using R = typename Prec<T>::R;
   __shared__ int vrows[2 * W];
@@ -805,6 +908,7 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
   }
   __syncthreads();
   const R zl = Prec<T>::zero_level(P);
+  const R tol2 = tol * tol;
   int step = 0;
   if (first_round) {
     // pairs inside each block: W - 1 rounds of W/2 pairs per block
@@ -812,13 +916,14 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
       int p, q;
       rr_pair(W, rr, warp % (W / 2), p, q);
       const int o = warp < W / 2 ? 0 : W;
-      block_local_round<T, W>(zl, xs, nrm, seq, step * W + warp, vrows, p + o, q + o, tau, &n_rot, &maxr_bits);
+      block_local_round<T, W>(tol2, zl, xs, nrm, seq, step * W + warp, vrows, p + o, q + o, tau, &n_rot,
+                              &maxr_bits);
     }
   }
   if (j_real) {
     for (int rr = 0; rr < W; ++rr, ++step)
-      block_local_round<T, W>(zl, xs, nrm, seq, step * W + warp, vrows, warp, W + (warp + rr) % W, tau, &n_rot,
-                              &maxr_bits);
+      block_local_round<T, W>(tol2, zl, xs, nrm, seq, step * W + warp, vrows, warp, W + (warp + rr) % W, tau,
+                              &n_rot, &maxr_bits);
   }
   // vectors back to global memory; norms for the tail rule
   for (int k = 0; k < 2 * W; ++k) {
@@ -833,14 +938,21 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
     atomicAdd(P.rotated, n_rot);
     atomicMax(P.maxr, maxr_bits);
   }
-  if (n_rot > 0 && !skip_acc) block_replay_acc<T, W>(P, vrows, seq, first_round, j_real);
+  if (n_rot > 0) {
+    if (acc_mode == 1) {
+      __syncthreads();  // xs is free: it holds D
+      block_correct_acc<T, W>(P, vrows, seq, first_round, j_real, reinterpret_cast<float2*>(xs));
+    } else {
+      block_replay_acc<T, W>(P, vrows, seq, first_round, j_real);
+    }
+  }
 }
 
 // All sweeps of one phase with the block order (see above); one CTA per SM.
-template <typename T, int W>
-__global__ void __launch_bounds__(32 * W, 1) svd_block_sweeps(const __grid_constant__ SvdBatch B, int nbpad_max,
-                                                             float stop, int max_sweeps, int fatal, int use_order,
-                                                             int skip_acc, double* work_flops) {
+template <typename T, int W, int MINB>
+__global__ void __launch_bounds__(32 * W, MINB) svd_block_sweeps(const __grid_constant__ SvdBatch B, int nbpad_max,
+                                                                float stop, double tol, int max_sweeps, int fatal,
+                                                                int use_order, int acc_mode, double* work_flops) {
   using C = BlockCfg<T, W>;
   using R = typename Prec<T>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -855,12 +967,26 @@ __global__ void __launch_bounds__(32 * W, 1) svd_block_sweeps(const __grid_const
       off[i + 1] = off[i] + (nb + (nb & 1)) / 2;
     }
   }
+  __shared__ int u_sh;
   __syncthreads();
   const int total = off[B.n];
   volatile unsigned* unconv = B.sync + 2;
+  // visits are handed out dynamically (their cost varies: the tail rule skips
+  // some, the first block round of a sweep adds the intra-block pairs) from
+  // two counters used in alternate block rounds: block 0 clears the other one
+  // while the current one is in use, and the grid barrier between rounds
+  // publishes the clearing.
+  unsigned* ctr = B.sync + 4;
+  int rnd = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int br = 0; br < nbpad_max - 1; ++br) {
-      for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    for (int br = 0; br < nbpad_max - 1; ++br, ++rnd) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(ctr + ((rnd + 1) & 1), 0u);
+      for (;;) {
+        __syncthreads();  // u_sh of the previous visit has been read
+        if (threadIdx.x == 0) u_sh = (int)atomicAdd(ctr + (rnd & 1), 1u);
+        __syncthreads();
+        const int u = u_sh;
+        if (u >= total) break;
         int pid = 0;
         while (u >= off[pid + 1]) ++pid;
         const SvdDesc& P = B.d[pid];
@@ -870,7 +996,7 @@ __global__ void __launch_bounds__(32 * W, 1) svd_block_sweeps(const __grid_const
         if (br >= nbp - 1) continue;
         int bi, bj;
         rr_pair(nbp, br, u - off[pid], bi, bj);
-        block_visit<T, W>(P, bi, bj, br == 0, use_order != 0, skip_acc != 0, xs, seq, nrm);
+        block_visit<T, W>(P, bi, bj, br == 0, use_order != 0, acc_mode, (R)tol, xs, seq, nrm);
       }
       if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
     }
@@ -1069,23 +1195,6 @@ __global__ void svd_truncate(const __grid_constant__ SvdBatch B) {
   *P.w = tail;
 }
 
-// Mode 1: the kept vectors in descending order, each divided by its norm
-// (rows of V^H), as the operand of the GEMM with theta; zero past chi.
-__global__ void svd_gather_kept(const __grid_constant__ SvdBatch B) {
-  const SvdDesc& P = B.d[blockIdx.y];
-  const int chi = *P.chi;
-  const int64_t n = (int64_t)P.kcap * P.len;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(idx / P.len), e = (int)(idx % P.len);
-    double2 v = make_double2(0.0, 0.0);
-    if (c < chi) {
-      const int i = P.perm[c];
-      v = zscale(P.X[(int64_t)i * P.len + e], 1.0 / P.sig[i]);
-    }
-    P.P[idx] = v;
-  }
-}
-
 __global__ void svd_write(const __grid_constant__ SvdBatch B) {
   const SvdDesc& P = B.d[blockIdx.y];
   const int chi = *P.chi;
@@ -1098,7 +1207,6 @@ __global__ void svd_write(const __grid_constant__ SvdBatch B) {
       const int i = P.perm[c];
       double2 v;
       if (P.trans) v = P.X[(int64_t)i * P.len + r];
-      else if (B.mode == 1) v = P.T[(int64_t)r * P.kcap + c];
       else v = zscale(zconj(P.Acc[(int64_t)i * P.n_vec + r]), P.sig[i]);
       P.PsiL[idx] = v;
     } else if (idx < nl + nr) {
@@ -1107,7 +1215,6 @@ __global__ void svd_write(const __grid_constant__ SvdBatch B) {
       const int i = P.perm[c];
       double2 v;
       if (!P.trans) v = P.X[(int64_t)i * P.len + col];
-      else if (B.mode == 1) v = P.T[(int64_t)c * P.cols + col];
       else v = zscale(zconj(P.Acc[(int64_t)i * P.n_vec + col]), P.sig[i]);
       P.PsiR[q] = v;
     } else {
@@ -1134,7 +1241,7 @@ static void jacobi_sweeps(SvdBatch& b, int npad_max, float stop, int fatal, cuda
   int total = 0;
   for (int i = 0; i < b.n; ++i) total += (b.d[i].n_vec + (b.d[i].n_vec & 1)) / 2;
   const int blocks = std::max(1, std::min(max_blocks, cdiv(total, SVD_WARPS)));
-  CUDA_TRY(cudaMemsetAsync(b.sync, 0, 4 * sizeof(unsigned), s));
+  CUDA_TRY(cudaMemsetAsync(b.sync, 0, 8 * sizeof(unsigned), s));
   int max_sweeps = SVD_MAX_SWEEPS;
   double* work_dev = nullptr;
   const double* work_host = prof_work_slot(&work_dev);
@@ -1144,20 +1251,23 @@ static void jacobi_sweeps(SvdBatch& b, int npad_max, float stop, int fatal, cuda
   ++g_launches;
 }
 
-// block sweeps (vectors of at most 512 elements); false if they cannot run
-template <typename T, int W>
-static bool block_sweeps(SvdBatch& b, float stop, int fatal, int use_order, int skip_acc, cudaStream_t s,
-                         const char* name) {
+// block sweeps (vectors of at most 512 elements) with up to MINB CTAs per SM;
+// false if they cannot run. tol: relative off-diagonal below which a pair is
+// left alone.
+template <typename T, int W, int MINB>
+static bool block_sweeps(SvdBatch& b, float stop, double tol, int fatal, int use_order, int acc_mode,
+                         cudaStream_t s, const char* name) {
   using C = BlockCfg<T, W>;
   static int max_blocks = -1;
   const size_t smem = block_smem_bytes<T, W>();
+  auto kern = svd_block_sweeps<T, W, MINB>;
   if (max_blocks < 0) {
     int dev = 0, sms = 0, per_sm = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CUDA_TRY(cudaFuncSetAttribute(svd_block_sweeps<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_block_sweeps<T, W>, C::THREADS, smem));
-    max_blocks = sms * std::min(per_sm, 1);
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, smem));
+    max_blocks = sms * std::min(per_sm, MINB);
   }
   if (max_blocks <= 0) return false;
   int total = 0, nbpad_max = 2;
@@ -1168,15 +1278,14 @@ static bool block_sweeps(SvdBatch& b, float stop, int fatal, int use_order, int 
     nbpad_max = std::max(nbpad_max, nb + (nb & 1));
   }
   const int blocks = std::max(1, std::min(max_blocks, total));
-  CUDA_TRY(cudaMemsetAsync(b.sync, 0, 4 * sizeof(unsigned), s));
+  CUDA_TRY(cudaMemsetAsync(b.sync, 0, 8 * sizeof(unsigned), s));
   int max_sweeps = SVD_MAX_SWEEPS;
   double* work_dev = nullptr;
   const double* work_host = prof_work_slot(&work_dev);
-  void* args[] = {(void*)&b,         (void*)&nbpad_max, (void*)&stop,     (void*)&max_sweeps,
-                  (void*)&fatal,     (void*)&use_order, (void*)&skip_acc, (void*)&work_dev};
+  void* args[] = {(void*)&b,     (void*)&nbpad_max, (void*)&stop,     (void*)&tol,     (void*)&max_sweeps,
+                  (void*)&fatal, (void*)&use_order, (void*)&acc_mode, (void*)&work_dev};
   ProfScope ps(name, s, 0.0, 0.0, work_host);
-  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)svd_block_sweeps<T, W>, dim3(blocks), dim3(C::THREADS), args,
-                                       smem, s));
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(C::THREADS), args, smem, s));
   ++g_launches;
   return true;
 }
@@ -1204,7 +1313,7 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   // FP32 phase: until the largest relative off-diagonal of a sweep is < 1e-4
   // (just above the FP32 rounding of the dot products); not converging here
   // only means a weaker preconditioner
-  if (!block_sweeps<float2, 16>(b, 1e-4f, 0, 0, 0, s, "svd_jacobi_fp32"))
+  if (!block_sweeps<float2, 16, 1>(b, 1e-4f, Prec<float2>::tol, 0, 0, 0, s, "svd_jacobi_fp32"))
     jacobi_sweeps<float2>(b, npad_max, 1e-4f, 0, s, "svd_jacobi_fp32");
   // ---- phase 2: unitary FP64 rotation and FP64 vectors ----
   svd_acc_to64<<<g1, 256, 0, s>>>(b);
@@ -1260,42 +1369,14 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   // stop after a sweep whose largest relative off-diagonal was below 1e-7 (full:
   // ~1e-14 left) or 1e-4 (mixed-precision sweeps: ~1e-8 or less left)
   const float stop64 = b.mode == 0 ? 1e-7f : 1e-4f;
-  if (!block_sweeps<double2, 8>(b, stop64, 1, 1, b.mode == 1 ? 1 : 0, s, "svd_jacobi_fp64"))
+  // mode 1 leaves pairs below 1e-10 alone (its target is ~1e-8)
+  const double tol64 = b.mode == 0 ? JACOBI_TOL : 1e-10;
+  if (!block_sweeps<double2, 8, 1>(b, stop64, tol64, 1, 1, b.mode == 1 ? 1 : 0, s, "svd_jacobi_fp64"))
     jacobi_sweeps<double2>(b, npad_max, stop64, 1, s, "svd_jacobi_fp64");
   svd_norms<<<gn, SVD_WARPS * 32, 0, s>>>(b);
   LAUNCH_CHECK();
   svd_truncate<<<b.n, 256, 0, s>>>(b);
   LAUNCH_CHECK();
-  if (b.mode == 1) {
-    // the other factor of the kept triplets from theta: U Lambda = theta V
-    // (vectors = rows) or Lambda V^H = U^H theta (vectors = columns)
-    int64_t kl_max = 1;
-    ZGemmBatch go{};
-    go.n = b.n;
-    for (int i = 0; i < b.n; ++i) {
-      SvdDesc& P = b.d[i];
-      P.kcap = std::min(P.chi_max, P.n_vec);
-      kl_max = std::max<int64_t>(kl_max, (int64_t)P.kcap * P.len);
-      ZGemmDesc& g = go.d[i];
-      g = ZGemmDesc{};
-      if (!P.trans) {  // C[r][c] = sum_e theta[r][e] conj(Xs[c][e])
-        g.M = P.rows; g.N = P.kcap; g.K = P.len;
-        g.A = P.theta; g.a_rs = P.cols; g.a_cs = 1;
-        g.B = P.P; g.b_rs = 1; g.b_cs = P.len; g.conj_b = 1;
-        g.C = P.T; g.c_rs = P.kcap; g.c_cs = 1;
-      } else {         // C[c][col] = sum_e conj(Xs[c][e]) theta[e][col]
-        g.M = P.kcap; g.N = P.cols; g.K = P.len;
-        g.A = P.P; g.a_rs = P.len; g.a_cs = 1; g.conj_a = 1;
-        g.B = P.theta; g.b_rs = P.cols; g.b_cs = 1;
-        g.C = P.T; g.c_rs = P.cols; g.c_cs = 1;
-      }
-    }
-    dim3 gg((unsigned)std::min<int64_t>(cdiv64(kl_max, 256), 152 * 8), b.n);
-    svd_gather_kept<<<gg, 256, 0, s>>>(b);
-    LAUNCH_CHECK();
-    ++g_launches;
-    launch_zgemm(go, s, "svd_vectors_zgemm");
-  }
   dim3 gw((unsigned)std::min<int64_t>(cdiv64(max_elems, 256), 152 * 8), b.n);
   svd_write<<<gw, 256, 0, s>>>(b);
   LAUNCH_CHECK();

@@ -28,15 +28,13 @@ struct SvdDesc {
   double* V;             // [chi]
   double2* PsiR;         // [chi][cols]
   double* s_sorted;      // [n_vec] all singular values, descending (may be null)
-  int kcap;              // min(chi_max, n_vec): columns of the mode-1 products (set by svd_split)
 };
 struct SvdBatch {
   int n;
-  int mode;              // 0: FP64 to ~1e-14 orthogonality; 1: to ~1e-8 or better (mixed-precision
-                         // sweeps), the FP64 sweeps leave Acc alone and the other factor comes from
-                         // one GEMM with theta (U Lambda = theta V, or Lambda V^H = U^H theta)
+  int mode;              // 0: FP64 to ~1e-14 orthogonality; 1: to ~1e-10, with the rotations of the
+                         // FP64 sweeps applied to Acc through an FP32-accumulated block rotation
   int* status;           // bit 8: NaN / zero state, 16: no convergence, 32: barrier timeout, 64: tail rule
-  unsigned* sync;        // 4 words of device scratch for the grid barrier and the sweep loop
+  unsigned* sync;        // 8 words of device scratch: grid barrier, sweep loop, visit counters
   SvdDesc d[MAXB];
 };
 
