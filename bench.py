@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--chi", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed steps of the plain FP64 GPU path (after one warm-up step); 0 skips it")
     ap.add_argument("--svd-case", type=int, default=0,
                     help="profiling case: two truncated splits of one N x N two-site state "
                          "(half the spectrum kept), no benchmark line")
@@ -201,11 +203,16 @@ def roofline(prof, steps, clk=None, kernel=None):
     peaks, src = measured_peaks()
     ms_launch = d["ms"] / max(d["launches"], 1)
     if dom.startswith("tc_gemm"):
-        # TF32 dense peak = measured bf16 burst x nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
-        peak = peaks["bf16_tflops"] * 1.1 / 2.25
+        # TF32 dense peak = measured bf16 burst x nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s);
+        # the 3xTF32 product issues three TF32 MMAs per algorithmic one, so its
+        # own peak in algorithmic flops is a third of that
+        tf32 = peaks["bf16_tflops"] * 1.1 / 2.25
+        passes = 3 if dom.endswith("x3") else 1
+        peak = tf32 / passes
         ach = d["flops"] / d["launches"] / (ms_launch * 1e-3) / 1e12
         r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-             "peak_source": "%s bf16 x 1.1/2.25 (TF32 nominal ratio)" % src}
+             "peak_source": "%s bf16 x 1.1/2.25 (TF32 nominal ratio)%s" % (src, " / 3 (3xTF32)" if passes == 3 else ""),
+             "tensor_pipe_frac": ach * passes / tf32}
     elif dom == "svd_jacobi_fp32":
         # FP32 ALU peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x clock
         mhz = (clk or {}).get("sm_mhz") or 2070.0
@@ -390,10 +397,46 @@ def run_ours(args, world, rank, local):
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
         "w_total": st.w_total, "chi_max_seen": st.chi_max_seen, "wall_s": wall,
     }
+    if args.fp64_steps > 0 and args.precision != "fp64":
+        ref = fp64_reference(args, tdvp, w, mpo, stream)
+        ref["speedup"] = value / ref["value"]
+        line["fp64_path"] = ref
     if not args.no_cpu_baseline:
         cb = cpu_baseline_sample(args.chi)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
+
+
+def fp64_reference(args, tdvp, w, mpo, stream):
+    """The plain FP64 GPU path on the same workload: time-steps/s over
+    --fp64-steps steps after one warm-up step (CUDA events on the stream), and
+    the largest difference of <sigma^z_j> between one mixed-precision step and
+    one FP64 step taken from the same seeded state."""
+    import torch
+    mdl, prm = w.model, w.params
+    raw = I.random_mps_tensors(mdl.N, args.chi, seed=0)
+    sz, out = {}, {}
+    for prec in (PREC[args.precision], I.FP64):
+        mps = tdvp.init_mps_tensors(raw, args.chi, 1e-14)
+        p = tdvp.step_params(dt=prm.dt, chi_max=args.chi, w_max=prm.w_max, eps=prm.eps,
+                             krylov_max=prm.krylov_max, krylov_tol=prm.krylov_tol, precision=prec,
+                             seg_len=prm.seg_len, merge_turning=1)
+        tdvp.step(mps, mpo, p, 1, stream=stream)
+        sz[prec] = tdvp.measure(mps, tdvp.OBS_SZ)
+        if prec == I.FP64:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            tdvp.step(mps, mpo, p, args.fp64_steps, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out = {"value": args.fp64_steps / (ms * 1e-3), "unit": UNIT, "steps": args.fp64_steps, "warmup": 1,
+                   "ms_per_step": ms / args.fp64_steps, "dtype": "f64"}
+        del mps
+    out["sigma_z_max_abs_diff_1_step"] = float(np.abs(sz[PREC[args.precision]] - sz[I.FP64]).max())
+    return out
 
 
 def state_gb(mdl, chi):

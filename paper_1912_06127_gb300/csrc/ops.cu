@@ -137,7 +137,7 @@ void Slot::ensure(int64_t vec, int64_t T, int64_t fsz, int64_t svd_n, int kmax_)
   sync = reinterpret_cast<unsigned*>(dalloc<int>(8));
   sig = dalloc<double>(nsvd + 3);
   perm = dalloc<int>(nsvd + 1);
-  rot = dalloc<int>(1);
+  rot = dalloc<int>(2);  // rotations, pairs checked
   conv = dalloc<int>(1);
 }
 

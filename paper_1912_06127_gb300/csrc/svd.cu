@@ -95,7 +95,7 @@ __global__ void svd_setup32(const __grid_constant__ SvdBatch B) {
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *P.rotated = 0;
+    P.rotated[0] = P.rotated[1] = 0;
     *P.conv = 0;
     *P.maxr = 0u;
   }
@@ -220,6 +220,7 @@ __device__ inline bool jacobi_params(const SvdDesc& P, typename Prec<T>::R a, ty
                                      typename Prec<T>::R kr, typename Prec<T>::R ki, int lane,
                                      typename Prec<T>::R& cs, T& m1, T& m2, typename Prec<T>::R& tk) {
   float ratio = 0.f;
+  if (lane == 0) atomicAdd(P.rotated + 1, 1);  // pairs checked
   if (!jacobi_rotation<T>(P, a, b, kr, ki, cs, m1, m2, tk, ratio)) return false;
   if (lane == 0) {
     atomicAdd(P.rotated, 1);
@@ -470,18 +471,21 @@ __device__ inline bool svd_tail_rule_holds(const SvdDesc& P) {
 // converged, resets the per-sweep counters and stores the number of
 // unconverged problems in sync[2].
 template <typename T>
-__device__ inline void sweep_end(const SvdBatch& B, float stop, double* work_flops) {
+__device__ inline void sweep_end(const SvdBatch& B, float stop, double* work_flops, int acc_in_phase) {
   unsigned cnt = 0;
   for (int i = 0; i < B.n; ++i) {
     const SvdDesc& P = B.d[i];
     if (!*P.conv) {
-      // work of this sweep: every pair's dots, and the rotations applied
+      // arithmetic of this sweep in the phase's precision: the cross product
+      // <x, y> of every pair checked (8 flops per element), the rotation of
+      // the vectors (20 per element) and, when it runs in this precision, of
+      // the rows of Acc
       if (work_flops) {
-        const double pairs = 0.5 * P.n_vec * (P.n_vec - 1);
-        work_flops[0] += 16.0 * P.len * pairs + 20.0 * (P.len + P.n_vec) * (double)*P.rotated;
+        const double per_rot = 20.0 * P.len + (acc_in_phase ? 20.0 * P.n_vec : 0.0);
+        work_flops[0] += 8.0 * P.len * (double)P.rotated[1] + per_rot * (double)P.rotated[0];
         work_flops[1] += 1.0;  // sweeps, summed over the problems of the batch
       }
-      bool done = *P.rotated == 0 || __uint_as_float(*P.maxr) < stop;
+      bool done = P.rotated[0] == 0 || __uint_as_float(*P.maxr) < stop;
       if constexpr (Prec<T>::tracks_norms) {
         // the estimate behind the tail rule failed: drop the rule and
         // sweep on until every pair is orthogonal
@@ -493,7 +497,7 @@ __device__ inline void sweep_end(const SvdBatch& B, float stop, double* work_flo
       if (done) *P.conv = 1;
       else ++cnt;
     }
-    *P.rotated = 0;
+    P.rotated[0] = P.rotated[1] = 0;
     *P.maxr = 0u;
   }
   *(volatile unsigned*)(B.sync + 2) = cnt;
@@ -535,7 +539,7 @@ __global__ void __launch_bounds__(SVD_WARPS * 32) svd_sweeps(const __grid_consta
       }
       if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_end<T>(B, stop, work_flops);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_end<T>(B, stop, work_flops, 1);
     if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
     if (*unconv == 0) return;
   }
@@ -650,7 +654,11 @@ __device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec
   using C = BlockCfg<T, W>;
   using R = typename Prec<T>::R;
   const int lane = threadIdx.x & 31;
-  const bool active = vrows[lp] >= 0 && vrows[lq] >= 0;
+  bool active = vrows[lp] >= 0 && vrows[lq] >= 0;
+  if constexpr (Prec<T>::tracks_norms) {
+    // tail rule: both vectors below the threshold -- not even the product is needed
+    if (active && tau > 0.0 && (double)nrm[lp] < tau * tau && (double)nrm[lq] < tau * tau) active = false;
+  }
   T* x = xs + lp * C::LMAX;
   T* y = xs + lq * C::LMAX;
   R kr = 0, ki = 0;
@@ -673,11 +681,10 @@ __device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec
     rec.m1f = rec.m2f = make_float2(0.f, 0.f);
     if (active) {
       const R a = nrm[lp], b = nrm[lq];
-      bool tail = false;
-      if constexpr (Prec<T>::tracks_norms) tail = tau > 0.0 && (double)a < tau * tau && (double)b < tau * tau;
       R a2, b2;
       float ratio = 0.f;
-      if (!tail && jacobi_rotation_fast<T>(tol2, zl, a, b, kr, ki, rec, a2, b2, ratio)) {
+      atomicAdd(n_rot + 1, 1);  // pairs checked
+      if (jacobi_rotation_fast<T>(tol2, zl, a, b, kr, ki, rec, a2, b2, ratio)) {
         rot = 1;
         rec.cm1 = (float)(rec.cs - R(1));
         rec.m1f = make_float2((float)rec.m1.x, (float)rec.m1.y);
@@ -855,7 +862,7 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
   using C = BlockCfg<T, W>;
   using R = typename Prec<T>::R;
   __shared__ int vrows[2 * W];
-  __shared__ int n_rot;
+  __shared__ int n_rot[2];  // rotations, pairs checked
   __shared__ unsigned maxr_bits;
   __shared__ int skip;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -868,7 +875,7 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
     vrows[tid] = (blk < nb && g < n) ? (use_order ? P.perm[g] : g) : -1;
   }
   if (tid == 0) {
-    n_rot = 0;
+    n_rot[0] = n_rot[1] = 0;
     maxr_bits = 0u;
     skip = 0;
   }
@@ -916,14 +923,14 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
       int p, q;
       rr_pair(W, rr, warp % (W / 2), p, q);
       const int o = warp < W / 2 ? 0 : W;
-      block_local_round<T, W>(tol2, zl, xs, nrm, seq, step * W + warp, vrows, p + o, q + o, tau, &n_rot,
+      block_local_round<T, W>(tol2, zl, xs, nrm, seq, step * W + warp, vrows, p + o, q + o, tau, n_rot,
                               &maxr_bits);
     }
   }
   if (j_real) {
     for (int rr = 0; rr < W; ++rr, ++step)
       block_local_round<T, W>(tol2, zl, xs, nrm, seq, step * W + warp, vrows, warp, W + (warp + rr) % W, tau,
-                              &n_rot, &maxr_bits);
+                              n_rot, &maxr_bits);
   }
   // vectors back to global memory; norms for the tail rule
   for (int k = 0; k < 2 * W; ++k) {
@@ -934,11 +941,14 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
   if constexpr (Prec<T>::tracks_norms) {
     if (tid < 2 * W && vrows[tid] >= 0) P.sig[vrows[tid]] = sqrt(fmax((double)nrm[tid], 0.0));
   }
-  if (tid == 0 && n_rot > 0) {
-    atomicAdd(P.rotated, n_rot);
-    atomicMax(P.maxr, maxr_bits);
+  if (tid == 0) {
+    if (n_rot[1] > 0) atomicAdd(P.rotated + 1, n_rot[1]);
+    if (n_rot[0] > 0) {
+      atomicAdd(P.rotated, n_rot[0]);
+      atomicMax(P.maxr, maxr_bits);
+    }
   }
-  if (n_rot > 0) {
+  if (n_rot[0] > 0) {
     if (acc_mode == 1) {
       __syncthreads();  // xs is free: it holds D
       block_correct_acc<T, W>(P, vrows, seq, first_round, j_real, reinterpret_cast<float2*>(xs));
@@ -1000,7 +1010,7 @@ __global__ void __launch_bounds__(32 * W, MINB) svd_block_sweeps(const __grid_co
       }
       if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_end<T>(B, stop, work_flops);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_end<T>(B, stop, work_flops, acc_mode == 0);
     if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
     if (*unconv == 0) return;
   }
@@ -1016,7 +1026,7 @@ __global__ void svd_acc_to64(const __grid_constant__ SvdBatch B) {
     P.Acc[i] = make_double2((double)a.x, (double)a.y);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *P.rotated = 0;
+    P.rotated[0] = P.rotated[1] = 0;
     *P.conv = 0;
     *P.maxr = 0u;
   }

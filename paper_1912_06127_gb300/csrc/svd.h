@@ -18,7 +18,7 @@ struct SvdDesc {
   unsigned* maxr;        // largest |<x,y>| / (|x| |y|) met in the current sweep (float bits)
   double* sig;           // [n_vec + 3] vector norms, then scale, ||theta||_F^2 and the tail threshold
   int* perm;             // [n_vec] descending order
-  int* rotated;          // rotations applied in the current sweep
+  int* rotated;          // [2]: rotations applied and pairs checked in the current sweep
   int* conv;             // 1 once a sweep applied no rotation
   int chi_max;
   double w_max, eps;
