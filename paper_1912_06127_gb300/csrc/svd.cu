@@ -112,12 +112,20 @@ __device__ inline float warp_sumf(float v) {
   return v;
 }
 
+// Element types of the Jacobi sweeps: double2 (complex FP64), float2 (complex
+// FP32) and float4 (complex double-float: re_hi, im_hi, re_lo, im_lo; value =
+// hi + lo, ~48 significant bits, computed on the FP32 pipe). R: Gram entries,
+// norms and rotation parameters; CT: complex rotation parameters; AT: the
+// element type of Acc.
 template <typename T>
 struct Prec;
 template <>
 struct Prec<double2> {
   using R = double;
+  using CT = double2;
+  using AT = double2;
   static constexpr double tol = JACOBI_TOL;
+  static constexpr bool dd = false;
   // pairs whose norms are both below 1e-14 ||theta||_F are rounding noise
   __device__ static R zero_level(const SvdDesc& P) { return 1e-28 * P.sig[P.n_vec + 1]; }
   // the FP64 phase tracks the vector norms in sig[0, n_vec) for the tail rule
@@ -126,10 +134,28 @@ struct Prec<double2> {
   __device__ static double2* X(const SvdDesc& P) { return P.X; }
   __device__ static double2* Acc(const SvdDesc& P) { return P.Acc; }
   __device__ static double2 mk(R a, R b) { return make_double2(a, b); }
+  __device__ static CT mkc(R a, R b) { return make_double2(a, b); }
+};
+template <>
+struct Prec<float4> {
+  using R = double;
+  using CT = double2;
+  using AT = double2;
+  static constexpr double tol = JACOBI_TOL;
+  static constexpr bool dd = true;
+  __device__ static R zero_level(const SvdDesc& P) { return 1e-28 * P.sig[P.n_vec + 1]; }
+  static constexpr bool tracks_norms = true;
+  __device__ static float4* X(const SvdDesc& P) { return reinterpret_cast<float4*>(P.X); }
+  __device__ static double2* Acc(const SvdDesc& P) { return P.Acc; }
+  __device__ static float4 mk(R, R) { return make_float4(0.f, 0.f, 0.f, 0.f); }  // zero only
+  __device__ static CT mkc(R a, R b) { return make_double2(a, b); }
 };
 template <>
 struct Prec<float2> {
   using R = float;
+  using CT = float2;
+  using AT = float2;
+  static constexpr bool dd = false;
   static constexpr float tol = 2e-6f;  // above the FP32 rounding of the dot products
   // FP32 noise level: 1e-6 ||theta||_F (theta scaled by sig[n_vec] in this phase)
   __device__ static R zero_level(const SvdDesc& P) {
@@ -141,7 +167,34 @@ struct Prec<float2> {
   __device__ static float2* X(const SvdDesc& P) { return P.X32; }
   __device__ static float2* Acc(const SvdDesc& P) { return P.Acc32; }
   __device__ static float2 mk(R a, R b) { return make_float2(a, b); }
+  __device__ static CT mkc(R a, R b) { return make_float2(a, b); }
 };
+
+// ---- double-float arithmetic (error-free transformations with FMA) ----
+// two_sum: s + e = a + b exactly; fast_two_sum needs |a| >= |b|.
+__device__ inline void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ inline void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+// compensated accumulation of (ah + al)(bh + bl) into the pair (s, c):
+// the leading product exactly (FMA), the cross terms in plain FP32
+__device__ inline void dd_acc(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p);
+  float t;
+  two_sum(s, p, s, t);
+  c += t + fmaf(ah, bl, fmaf(al, bh, e));
+}
+// double -> (hi, lo) floats
+__device__ inline float2 dd_split(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
 
 template <typename T>
 __device__ inline void rot2(T* x, T* y, int n, int lane, typename Prec<T>::R cs, T m1, T m2) {
@@ -573,7 +626,7 @@ struct BlockCfg {
 template <typename T>
 struct RotRec {
   typename Prec<T>::R cs;
-  T m1, m2;  // identity rotation: cs = 1, m1 = m2 = 0
+  typename Prec<T>::CT m1, m2;  // identity rotation: cs = 1, m1 = m2 = 0
   // FP32 copies for the accumulation of the block rotation in FP32 (cm1 = cs - 1)
   float cm1;
   float2 m1f, m2f;
@@ -629,8 +682,8 @@ __device__ inline bool jacobi_rotation_fast(typename Prec<T>::R tol2, typename P
   const R phr = kr * rk, phi = ki * rk;
   // x' = cs x - sn e^{-i phi} y ; y' = sn e^{i phi} x + cs y
   rec.cs = cs;
-  rec.m1 = Prec<T>::mk(-sn * phr, sn * phi);
-  rec.m2 = Prec<T>::mk(sn * phr, sn * phi);
+  rec.m1 = Prec<T>::mkc(-sn * phr, sn * phi);
+  rec.m2 = Prec<T>::mkc(sn * phr, sn * phi);
   // |x'|^2 = cs^2 (a + t^2 b - 2 t |k|), |y'|^2 = cs^2 (b + t^2 a + 2 t |k|)
   const R c2 = cs * cs;
   a2 = c2 * (a + t * t * b - R(2) * t * ak);
@@ -645,12 +698,66 @@ __device__ inline void apply_rot(T& u, T& v, const RotRec<T>& r) {
   v = Prec<T>::mk(r.cs * y.x + r.m2.x * x.x - r.m2.y * x.y, r.cs * y.y + r.m2.x * x.y + r.m2.y * x.x);
 }
 
+// Cross product <x, y> of two vectors in shared memory, summed over the warp.
+template <typename T, int W>
+__device__ inline void block_cross(const T* x, const T* y, int lane, typename Prec<T>::R& kr,
+                                   typename Prec<T>::R& ki) {
+  using C = BlockCfg<T, W>;
+  using R = typename Prec<T>::R;
+  if constexpr (Prec<T>::dd) {
+    // compensated sums (the leading products exact, the rest in FP32): the
+    // result carries ~48 bits, as if summed in double-float
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < C::EPT; ++i) {
+      const float4 u = x[lane + 32 * i], v = y[lane + 32 * i];
+      dd_acc(sr, cr, u.x, u.z, v.x, v.z);    // re(u) re(v)
+      dd_acc(sr, cr, u.y, u.w, v.y, v.w);    // im(u) im(v)
+      dd_acc(si, ci, u.x, u.z, v.y, v.w);    // re(u) im(v)
+      dd_acc(si, ci, -u.y, -u.w, v.x, v.z);  // -im(u) re(v)
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, sr, o), c2 = __shfl_xor_sync(0xffffffffu, cr, o);
+      const float s3 = __shfl_xor_sync(0xffffffffu, si, o), c3 = __shfl_xor_sync(0xffffffffu, ci, o);
+      float t;
+      two_sum(sr, s2, sr, t);
+      cr += c2 + t;
+      two_sum(si, s3, si, t);
+      ci += c3 + t;
+    }
+    kr = (R)sr + (R)cr;
+    ki = (R)si + (R)ci;
+  } else {
+    R a = 0, b = 0;
+#pragma unroll
+    for (int i = 0; i < C::EPT; ++i) {
+      const T u = x[lane + 32 * i], v = y[lane + 32 * i];
+      a += u.x * v.x + u.y * v.y;  // conj(u) v
+      b += u.x * v.y - u.y * v.x;
+    }
+    kr = Prec<T>::wsum(a);
+    ki = Prec<T>::wsum(b);
+  }
+}
+
+// o = x + sum_k p_k q_k in double-float (x, p_k, q_k given as hi/lo pairs)
+__device__ inline void dd_axpy3(float xh, float xl, float p1h, float p1l, float q1h, float q1l, float p2h,
+                                float p2l, float q2h, float q2l, float p3h, float p3l, float q3h, float q3l,
+                                float& oh, float& ol) {
+  float s = xh, c = xl;
+  dd_acc(s, c, p1h, p1l, q1h, q1l);
+  dd_acc(s, c, p2h, p2l, q2h, q2l);
+  dd_acc(s, c, p3h, p3l, q3h, q3l);
+  fast_two_sum(s, c, oh, ol);
+}
+
 // One local round: warp w rotates local vectors (lp, lq); every thread of the
 // CTA calls it (it ends with a barrier).
 template <typename T, int W>
-__device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec<T>::R zl, T* xs, typename Prec<T>::R* nrm, RotRec<T>* seq,
-                                         int slot, const int* vrows, int lp, int lq, double tau, int* n_rot,
-                                         unsigned* maxr_bits) {
+__device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec<T>::R zl, T* xs,
+                                         typename Prec<T>::R* nrm, RotRec<T>* seq, int slot, const int* vrows,
+                                         int lp, int lq, double tau, int* n_rot, unsigned* maxr_bits) {
   using C = BlockCfg<T, W>;
   using R = typename Prec<T>::R;
   const int lane = threadIdx.x & 31;
@@ -662,21 +769,12 @@ __device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec
   T* x = xs + lp * C::LMAX;
   T* y = xs + lq * C::LMAX;
   R kr = 0, ki = 0;
-  if (active) {
-#pragma unroll
-    for (int i = 0; i < C::EPT; ++i) {
-      const T u = x[lane + 32 * i], v = y[lane + 32 * i];
-      kr += u.x * v.x + u.y * v.y;  // conj(u) v
-      ki += u.x * v.y - u.y * v.x;
-    }
-  }
-  kr = Prec<T>::wsum(kr);
-  ki = Prec<T>::wsum(ki);
+  if (active) block_cross<T, W>(x, y, lane, kr, ki);
   RotRec<T> rec;
   int rot = 0;
   if (lane == 0) {
     rec.cs = 1;
-    rec.m1 = rec.m2 = Prec<T>::mk(0, 0);
+    rec.m1 = rec.m2 = Prec<T>::mkc(0, 0);
     rec.cm1 = 0.f;
     rec.m1f = rec.m2f = make_float2(0.f, 0.f);
     if (active) {
@@ -699,17 +797,52 @@ __device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec
   }
   rot = __shfl_sync(0xffffffffu, rot, 0);
   if (rot) {
-    rec.cs = __shfl_sync(0xffffffffu, rec.cs, 0);
-    rec.m1.x = __shfl_sync(0xffffffffu, rec.m1.x, 0);
-    rec.m1.y = __shfl_sync(0xffffffffu, rec.m1.y, 0);
-    rec.m2.x = __shfl_sync(0xffffffffu, rec.m2.x, 0);
-    rec.m2.y = __shfl_sync(0xffffffffu, rec.m2.y, 0);
+    if constexpr (Prec<T>::dd) {
+      // x' = x + [(cs - 1) x + m1 y], y' = y + [(cs - 1) y + m2 x] in double-float
+      float2 c1 = make_float2(0.f, 0.f), a1 = c1, b1 = c1, a2 = c1, b2 = c1;  // hi/lo of cs-1, m1, m2
+      if (lane == 0) {
+        c1 = dd_split(rec.cs - 1.0);
+        a1 = dd_split(rec.m1.x);
+        b1 = dd_split(rec.m1.y);
+        a2 = dd_split(rec.m2.x);
+        b2 = dd_split(rec.m2.y);
+      }
+      c1.x = __shfl_sync(0xffffffffu, c1.x, 0);
+      c1.y = __shfl_sync(0xffffffffu, c1.y, 0);
+      a1.x = __shfl_sync(0xffffffffu, a1.x, 0);
+      a1.y = __shfl_sync(0xffffffffu, a1.y, 0);
+      b1.x = __shfl_sync(0xffffffffu, b1.x, 0);
+      b1.y = __shfl_sync(0xffffffffu, b1.y, 0);
+      a2.x = __shfl_sync(0xffffffffu, a2.x, 0);
+      a2.y = __shfl_sync(0xffffffffu, a2.y, 0);
+      b2.x = __shfl_sync(0xffffffffu, b2.x, 0);
+      b2.y = __shfl_sync(0xffffffffu, b2.y, 0);
+#pragma unroll 2
+      for (int i = 0; i < C::EPT; ++i) {
+        const float4 u = x[lane + 32 * i], v = y[lane + 32 * i];
+        float4 nu, nv;
+        // re x' = re u + c1 re u + a1 re v - b1 im v ; im x' = im u + c1 im u + a1 im v + b1 re v
+        dd_axpy3(u.x, u.z, c1.x, c1.y, u.x, u.z, a1.x, a1.y, v.x, v.z, -b1.x, -b1.y, v.y, v.w, nu.x, nu.z);
+        dd_axpy3(u.y, u.w, c1.x, c1.y, u.y, u.w, a1.x, a1.y, v.y, v.w, b1.x, b1.y, v.x, v.z, nu.y, nu.w);
+        // re y' = re v + c1 re v + a2 re u - b2 im u ; im y' = im v + c1 im v + a2 im u + b2 re u
+        dd_axpy3(v.x, v.z, c1.x, c1.y, v.x, v.z, a2.x, a2.y, u.x, u.z, -b2.x, -b2.y, u.y, u.w, nv.x, nv.z);
+        dd_axpy3(v.y, v.w, c1.x, c1.y, v.y, v.w, a2.x, a2.y, u.y, u.w, b2.x, b2.y, u.x, u.z, nv.y, nv.w);
+        x[lane + 32 * i] = nu;
+        y[lane + 32 * i] = nv;
+      }
+    } else {
+      rec.cs = __shfl_sync(0xffffffffu, rec.cs, 0);
+      rec.m1.x = __shfl_sync(0xffffffffu, rec.m1.x, 0);
+      rec.m1.y = __shfl_sync(0xffffffffu, rec.m1.y, 0);
+      rec.m2.x = __shfl_sync(0xffffffffu, rec.m2.x, 0);
+      rec.m2.y = __shfl_sync(0xffffffffu, rec.m2.y, 0);
 #pragma unroll
-    for (int i = 0; i < C::EPT; ++i) {
-      T u = x[lane + 32 * i], v = y[lane + 32 * i];
-      apply_rot<T>(u, v, rec);
-      x[lane + 32 * i] = u;
-      y[lane + 32 * i] = v;
+      for (int i = 0; i < C::EPT; ++i) {
+        T u = x[lane + 32 * i], v = y[lane + 32 * i];
+        apply_rot<T>(u, v, rec);
+        x[lane + 32 * i] = u;
+        y[lane + 32 * i] = v;
+      }
     }
   }
   __syncthreads();
@@ -823,14 +956,15 @@ __device__ inline void block_correct_acc(const SvdDesc& P, const int* vrows, con
     for (int k = 0; k < N2; ++k) D[k * N2 + j] = col[k];
   }
   __syncthreads();
-  T* A = Prec<T>::Acc(P);
+  using AT = typename Prec<T>::AT;
+  AT* A = Prec<T>::Acc(P);
   const int n = P.n_vec;
   for (int c = tid; c < n; c += C::THREADS) {
     float2 af[N2];
 #pragma unroll
     for (int k = 0; k < N2; ++k) {
       const int r = vrows[k];
-      const T a = r >= 0 ? A[(int64_t)r * n + c] : Prec<T>::mk(0, 0);
+      const AT a = r >= 0 ? A[(int64_t)r * n + c] : AT{};
       af[k] = make_float2((float)a.x, (float)a.y);
     }
 #pragma unroll
@@ -844,7 +978,7 @@ __device__ inline void block_correct_acc(const SvdDesc& P, const int* vrows, con
         s.x = fmaf(d.x, af[jj].x, fmaf(-d.y, af[jj].y, s.x));
         s.y = fmaf(d.x, af[jj].y, fmaf(d.y, af[jj].x, s.y));
       }
-      T a = A[(int64_t)r * n + c];
+      AT a = A[(int64_t)r * n + c];
       a.x += s.x;
       a.y += s.y;
       A[(int64_t)r * n + c] = a;
@@ -904,14 +1038,9 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
   __syncthreads();
   // squared norms, a warp per vector
   for (int k = warp; k < 2 * W; k += W) {
-    R s2 = 0;
-#pragma unroll
-    for (int i = 0; i < C::EPT; ++i) {
-      const T u = xs[k * C::LMAX + lane + 32 * i];
-      s2 += u.x * u.x + u.y * u.y;
-    }
-    s2 = Prec<T>::wsum(s2);
-    if (lane == 0) nrm[k] = s2;
+    R kr, ki;
+    block_cross<T, W>(xs + k * C::LMAX, xs + k * C::LMAX, lane, kr, ki);
+    if (lane == 0) nrm[k] = kr;
   }
   __syncthreads();
   const R zl = Prec<T>::zero_level(P);
@@ -949,10 +1078,10 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
     }
   }
   if (n_rot[0] > 0) {
-    if (acc_mode == 1) {
+    if (acc_mode == 1 || Prec<T>::dd) {
       __syncthreads();  // xs is free: it holds D
       block_correct_acc<T, W>(P, vrows, seq, first_round, j_real, reinterpret_cast<float2*>(xs));
-    } else {
+    } else if constexpr (!Prec<T>::dd) {
       block_replay_acc<T, W>(P, vrows, seq, first_round, j_real);
     }
   }
@@ -1015,6 +1144,25 @@ __global__ void __launch_bounds__(32 * W, MINB) svd_block_sweeps(const __grid_co
     if (*unconv == 0) return;
   }
   if (fatal && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, 16);
+}
+
+// The FP64 vectors to double-float and back, in place (16 bytes either way).
+__global__ void svd_x_to_dd(const __grid_constant__ SvdBatch B) {
+  const SvdDesc& P = B.d[blockIdx.y];
+  const int64_t n = (int64_t)P.n_vec * P.len;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = P.X[i];
+    const float2 re = dd_split(v.x), im = dd_split(v.y);
+    reinterpret_cast<float4*>(P.X)[i] = make_float4(re.x, im.x, re.y, im.y);
+  }
+}
+__global__ void svd_dd_to_x(const __grid_constant__ SvdBatch B) {
+  const SvdDesc& P = B.d[blockIdx.y];
+  const int64_t n = (int64_t)P.n_vec * P.len;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = reinterpret_cast<const float4*>(P.X)[i];
+    P.X[i] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  }
 }
 
 // FP32 rotation -> FP64; reset the convergence state for the FP64 phase
@@ -1381,8 +1529,20 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   const float stop64 = b.mode == 0 ? 1e-7f : 1e-4f;
   // mode 1 leaves pairs below 1e-10 alone (its target is ~1e-8)
   const double tol64 = b.mode == 0 ? JACOBI_TOL : 1e-10;
-  if (!block_sweeps<double2, 8, 1>(b, stop64, tol64, 1, 1, b.mode == 1 ? 1 : 0, s, "svd_jacobi_fp64"))
+  bool short_rows = true;
+  for (int i = 0; i < b.n; ++i) short_rows = short_rows && b.d[i].len <= BlockCfg<float4, 8>::LMAX;
+  if (b.mode == 1 && short_rows) {
+    // mixed mode: the final sweeps in double-float on the FP32 pipe (~48 bits,
+    // ample for its 1e-10 tolerance), Acc updated through FP32 block rotations
+    svd_x_to_dd<<<g1, 256, 0, s>>>(b);
+    LAUNCH_CHECK();
+    if (!block_sweeps<float4, 8, 1>(b, stop64, tol64, 1, 1, 1, s, "svd_jacobi_dd")) fail(TDVP_ECUDA, "block sweeps");
+    svd_dd_to_x<<<g1, 256, 0, s>>>(b);
+    LAUNCH_CHECK();
+    g_launches += 2;
+  } else if (!block_sweeps<double2, 8, 1>(b, stop64, tol64, 1, 1, b.mode == 1 ? 1 : 0, s, "svd_jacobi_fp64")) {
     jacobi_sweeps<double2>(b, npad_max, stop64, 1, s, "svd_jacobi_fp64");
+  }
   svd_norms<<<gn, SVD_WARPS * 32, 0, s>>>(b);
   LAUNCH_CHECK();
   svd_truncate<<<b.n, 256, 0, s>>>(b);
