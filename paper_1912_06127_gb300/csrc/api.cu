@@ -353,7 +353,9 @@ void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, con
     q.c_rs = (int64_t)d * B;
     q.c_cs = 1;
   }
-  launch_zgemm(g, s, "theta_form_zgemm");
+  // the mixed path forms Theta in double-float (~48 bits, on the FP32 pipe)
+  if (prec == TDVP_FP64) launch_zgemm(g, s, "theta_form_zgemm");
+  else launch_zgemm_dd(g, s, "theta_form_dd");
   // exp(-i H2_eff t) Theta
   std::vector<MvProb> P(n);
   std::vector<const double2*> x(n);

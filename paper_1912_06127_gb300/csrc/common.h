@@ -77,6 +77,34 @@ __host__ __device__ inline void cfma(float2& a, float2 b, float2 c) {
   a.y = fmaf(b.y, c.x, a.y);
 }
 
+// ---- double-float arithmetic (error-free transformations with FMA) ----
+// A double-float value is hi + lo with two FP32 numbers (~48 significant
+// bits); on GB300 it is computed on the FP32 pipe, 64x wider than FP64.
+// two_sum: s + e = a + b exactly; fast_two_sum needs |a| >= |b|.
+__device__ inline void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ inline void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+// compensated accumulation of (ah + al)(bh + bl) into the pair (s, c): the
+// leading product exactly (FMA), the cross terms in plain FP32
+__device__ inline void dd_acc(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p);
+  float t;
+  two_sum(s, p, s, t);
+  c += t + fmaf(ah, bl, fmaf(al, bh, e));
+}
+// double -> (hi, lo) floats
+__device__ inline float2 dd_split(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
 inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -104,6 +132,10 @@ struct ZGemmBatch {
   ZGemmDesc d[MAXB];
 };
 void launch_zgemm(const ZGemmBatch& b, cudaStream_t s, const char* prof_name = "zgemm_fp64");
+// The same product with double-float arithmetic on the FP32 pipe (inputs
+// rounded to ~48 bits, compensated accumulation): for the mixed-precision
+// path, where ~1e-14 relative accuracy is ample.
+void launch_zgemm_dd(const ZGemmBatch& b, cudaStream_t s, const char* prof_name = "zgemm_dd");
 
 // ---------------------------------------------------------------------------
 // Sparse MPO operator applied in the "W stage" of a contraction:

@@ -131,6 +131,138 @@ void launch_zgemm(const ZGemmBatch& b, cudaStream_t s, const char* prof_name) {
 }
 
 // ---------------------------------------------------------------------------
+// Complex GEMM in double-float: the zgemm_kernel tiling, operands converted to
+// (hi, lo) pairs when staged in shared memory, each product's leading term
+// exact through FMA and accumulated with two_sum, the small terms in FP32.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ ZGemmBatch batch) {
+  const int pid = blockIdx.y;
+  if (pid >= batch.n) return;
+  const ZGemmDesc& P = batch.d[pid];
+  if (P.skip && *P.skip) return;
+  const int tiles_m = (P.M + ZG_BM - 1) / ZG_BM;
+  const int tiles_n = (P.N + ZG_BN - 1) / ZG_BN;
+  if ((int)blockIdx.x >= tiles_m * tiles_n) return;
+  const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  if (P.upper_only && tm > tn) return;
+  const int m0 = tm * ZG_BM, n0 = tn * ZG_BN;
+  __shared__ float4 As[ZG_BK][ZG_BM];  // (re_hi, im_hi, re_lo, im_lo)
+  __shared__ float4 Bs[ZG_BK][ZG_BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  float sr[4][4], cr[4][4], si[4][4], ci[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sr[i][j] = cr[i][j] = si[i][j] = ci[i][j] = 0.f;
+  const bool a_k_fast = (P.a_cs == 1);
+  const bool b_n_fast = (P.b_cs == 1);
+  for (int k0 = 0; k0 < P.K; k0 += ZG_BK) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int e = tid + r * 256;
+      int i, k;
+      if (a_k_fast) {
+        k = e % ZG_BK;
+        i = e / ZG_BK;
+      } else {
+        i = e % ZG_BM;
+        k = e / ZG_BM;
+      }
+      double2 v = make_double2(0.0, 0.0);
+      int gi = m0 + i, gk = k0 + k;
+      if (gi < P.M && gk < P.K) {
+        v = P.A[(int64_t)gi * P.a_rs + (int64_t)gk * P.a_cs];
+        if (P.conj_a) v.y = -v.y;
+        if (P.kscale) {
+          double sc = P.kscale[gk];
+          v.x *= sc;
+          v.y *= sc;
+        }
+      }
+      {
+        const float2 re = dd_split(v.x), im = dd_split(v.y);
+        As[k][i] = make_float4(re.x, im.x, re.y, im.y);
+      }
+      int j, kb;
+      if (b_n_fast) {
+        j = e % ZG_BN;
+        kb = e / ZG_BN;
+      } else {
+        kb = e % ZG_BK;
+        j = e / ZG_BK;
+      }
+      double2 w = make_double2(0.0, 0.0);
+      int gj = n0 + j, gkb = k0 + kb;
+      if (gj < P.N && gkb < P.K) {
+        w = P.B[(int64_t)gkb * P.b_rs + (int64_t)gj * P.b_cs];
+        if (P.conj_b) w.y = -w.y;
+      }
+      {
+        const float2 re = dd_split(w.x), im = dd_split(w.y);
+        Bs[kb][j] = make_float4(re.x, im.x, re.y, im.y);
+      }
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < ZG_BK; ++kk) {
+      float4 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          // re += a.re b.re - a.im b.im ; im += a.re b.im + a.im b.re
+          dd_acc(sr[i][j], cr[i][j], a[i].x, a[i].z, b[j].x, b[j].z);
+          dd_acc(sr[i][j], cr[i][j], -a[i].y, -a[i].w, b[j].y, b[j].w);
+          dd_acc(si[i][j], ci[i][j], a[i].x, a[i].z, b[j].y, b[j].w);
+          dd_acc(si[i][j], ci[i][j], a[i].y, a[i].w, b[j].x, b[j].z);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gi = m0 + ty + 16 * i;
+    if (gi >= P.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gj = n0 + tx + 16 * j;
+      if (gj >= P.N) continue;
+      double2* c = P.C + (int64_t)gi * P.c_rs + (int64_t)gj * P.c_cs;
+      double2 v = make_double2((double)sr[i][j] + (double)cr[i][j], (double)si[i][j] + (double)ci[i][j]);
+      if (P.accumulate) v = zadd(v, *c);
+      *c = v;
+    }
+  }
+}
+
+void launch_zgemm_dd(const ZGemmBatch& b, cudaStream_t s, const char* prof_name) {
+  if (b.n <= 0) return;
+  int maxt = 0;
+  for (int i = 0; i < b.n; ++i) {
+    const auto& d = b.d[i];
+    if (d.M <= 0 || d.N <= 0) continue;
+    maxt = std::max(maxt, cdiv(d.M, ZG_BM) * cdiv(d.N, ZG_BN));
+  }
+  if (maxt == 0) return;
+  double fl = 0, by = 0;
+  for (int i = 0; i < b.n; ++i) {
+    const auto& d = b.d[i];
+    fl += (d.upper_only ? 4.0 : 8.0) * d.M * d.N * d.K;
+    by += 16.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
+  }
+  ProfScope ps(prof_name, s, fl, by);
+  dim3 grid(maxt, b.n);
+  zgemm_dd_kernel<<<grid, 256, 0, s>>>(b);
+  LAUNCH_CHECK();
+  ++g_launches;
+}
+
+// ---------------------------------------------------------------------------
 // W stage: Y[a, w', S, b] = sum_{w, S'} Wop[w, w', S, S'] X[a, w, S', b].
 // One thread per output element, b fastest; the block list of each w' is
 // read from global memory (a few KB, cached).

@@ -170,31 +170,7 @@ struct Prec<float2> {
   __device__ static CT mkc(R a, R b) { return make_float2(a, b); }
 };
 
-// ---- double-float arithmetic (error-free transformations with FMA) ----
-// two_sum: s + e = a + b exactly; fast_two_sum needs |a| >= |b|.
-__device__ inline void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-__device__ inline void fast_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  e = b - (s - a);
-}
-// compensated accumulation of (ah + al)(bh + bl) into the pair (s, c):
-// the leading product exactly (FMA), the cross terms in plain FP32
-__device__ inline void dd_acc(float& s, float& c, float ah, float al, float bh, float bl) {
-  const float p = ah * bh;
-  const float e = fmaf(ah, bh, -p);
-  float t;
-  two_sum(s, p, s, t);
-  c += t + fmaf(ah, bl, fmaf(al, bh, e));
-}
-// double -> (hi, lo) floats
-__device__ inline float2 dd_split(double x) {
-  const float h = (float)x;
-  return make_float2(h, (float)(x - (double)h));
-}
+
 
 template <typename T>
 __device__ inline void rot2(T* x, T* y, int n, int lane, typename Prec<T>::R cs, T m1, T m2) {
@@ -1500,7 +1476,8 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   // Newton-Schulz steps: unitarity error ~1e-5 (FP32 rotations) -> ~1e-10 -> ~1e-16
   const int ns_steps = b.mode == 0 ? 2 : 1;
   for (int it = 0; it < ns_steps; ++it) {
-    launch_zgemm(gp, s, "svd_newton_schulz");
+    if (b.mode == 1) launch_zgemm_dd(gp, s, "svd_newton_schulz_dd");
+    else launch_zgemm(gp, s, "svd_newton_schulz");
     const int nt = cdiv(nvec_max, NS_T);
     {
       double fl = 0.0;
@@ -1514,7 +1491,8 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
     LAUNCH_CHECK();
     g_launches += 2;
   }
-  launch_zgemm(gx, s, "svd_newton_schulz");
+  if (b.mode == 1) launch_zgemm_dd(gx, s, "svd_newton_schulz_dd");
+  else launch_zgemm(gx, s, "svd_newton_schulz");
   g_launches += 2;
   // ---- phase 3: FP64 sweeps ----
   dim3 gn(cdiv(nvec_max, SVD_WARPS), b.n);
