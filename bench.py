@@ -107,6 +107,12 @@ def allreduce_max(x, world):
     return float(t.item())
 
 
+def job_value(steps, ms_max, world):
+    """Whole-job throughput of `world` replicas that each ran `steps` steps,
+    the slowest taking ms_max milliseconds."""
+    return steps * world / (ms_max * 1e-3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -367,8 +373,7 @@ def run_ours(args, world, rank, local):
     e2e_s = allreduce_max((time.perf_counter() - t0) / n_e2e, world)
     if rank != 0:
         return
-    steps_all = args.steps * world
-    value = steps_all / (ms_max * 1e-3)
+    value = job_value(args.steps, ms_max, world)
     rl, dom = roofline(prof, args.steps, clk)
     tc_kind = "tc_gemm_tf32x3" if args.precision == "tf32x3" else "tc_gemm_tf32"
     rl_heff, _ = roofline(prof, args.steps, clk, tc_kind) if tc_kind in prof else (None, None)
