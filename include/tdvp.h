@@ -179,6 +179,41 @@ void tdvp_free_mps(tdvp_mps mps);
 int tdvp_step(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps,
               tdvp_step_stats* stats, void* stream);
 
+/* ---- ground states: two-site DMRG ----
+ * The paper prepares its initial states with two-site DMRG (Sec. IV and the
+ * Supplemental Material) and notes that a TDVP time step has the sweep
+ * pattern and cost of a two-site DMRG sweep (Sec. III A); it prints no DMRG
+ * algorithm, so this is the textbook two-site update built from the same
+ * pieces as tdvp_step: Theta = Psi_j V_j Psi_{j+1}, the lowest eigenvector of
+ * H2_eff by Lanczos on the tridiagonal projection (at most krylov_max vectors
+ * started from Theta, stopped when the residual estimate beta_{k} |z_{k-1}|
+ * falls below krylov_tol or on breakdown; the new Theta keeps the norm of the
+ * old), the truncated split of Fig. 5 and the environment update of the sweep
+ * direction. No backward one-site step. */
+typedef struct {
+  int chi_max;
+  double w_max;
+  double eps;
+  int krylov_max;      /* <= 24 */
+  double krylov_tol;   /* 0: always krylov_max vectors */
+  int precision;       /* TDVP_FP64, TDVP_TF32 or TDVP_TF32X3 (as tdvp_step) */
+} tdvp_dmrg_params;
+
+typedef struct {
+  double energy;             /* Ritz value of the last local update (the state's energy) */
+  double w_total;            /* discarded weight summed over all splits             */
+  int chi_max_seen;
+  int64_t krylov_vectors;
+  int64_t n_updates;         /* two-site updates                                    */
+  int64_t kernel_launches;
+} tdvp_dmrg_stats;
+
+/* n_sweeps serial sweeps (left to right over pairs 0..N-2, then right to left)
+ * on `mps` in place. Environments are built as in tdvp_step (and cached in the
+ * handle). Synchronises `stream` after every update. Errors as tdvp_step. */
+int tdvp_dmrg(tdvp_mps mps, tdvp_mpo mpo, const tdvp_dmrg_params* params, int n_sweeps,
+              tdvp_dmrg_stats* stats, void* stream);
+
 /* ---- measurement (Sec. IV; excluded from timing as in the paper) ---- */
 
 /* <psi|O_j|psi>/<psi|psi> for every site j (N doubles) by full transfer-matrix

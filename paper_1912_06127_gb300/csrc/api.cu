@@ -324,8 +324,12 @@ struct StageOp {
   int j, tfac, env;
 };
 
+// Two-site updates of one stage. ground = false: Theta' = exp(-i H2_eff t) Theta
+// (Eq. 18); ground = true: Theta' = the lowest Ritz vector of H2_eff in the
+// Krylov space of Theta (two-site DMRG), its Ritz value written to *energy
+// (one problem).
 void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, const tdvp_step_params* p,
-              tdvp_step_stats* st, cudaStream_t s) {
+              tdvp_step_stats* st, cudaStream_t s, bool ground = false, double* energy = nullptr) {
   const int n = (int)ops.size();
   const int d = S->d, m = M->m, prec = p->precision;
   const double tau = 0.5 * p->dt;
@@ -376,7 +380,14 @@ void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, con
     t[i] = ops[i].tfac * tau;
     if (st) st->heff_flops += p->krylov_max * heff_flops(A, B, d * d, m, M->w2.nnz);
   }
-  expm_batch(P, x, y, t, p->krylov_max, p->krylov_tol, c);
+  expm_batch(P, x, y, t, p->krylov_max, p->krylov_tol, c, ground);
+  if (ground && energy) {
+    LzState h{};
+    CUDA_TRY(cudaMemcpyAsync(&h, sl[0]->st, sizeof(LzState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *energy = h.energy;
+    if (st) st->krylov_vectors += h.nvec_used;
+  }
   // truncated SVD re-split (Fig. 5)
   SvdBatch sb{};
   sb.n = n;
@@ -518,6 +529,41 @@ void step_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_st
   }
   if (st) {
     st->kernel_launches += g_launches - l0;
+  }
+}
+
+// Two-site DMRG sweeps: left to right over the pairs (rebuilding left
+// environments), then right to left (rebuilding right environments), each
+// update replacing Theta by the lowest eigenvector of H2_eff.
+void dmrg_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_dmrg_params* dp, int n_sweeps, tdvp_dmrg_stats* ds,
+               cudaStream_t s) {
+  if (!dp) fail(TDVP_EINVAL, "params is NULL");
+  tdvp_step_params p{};
+  p.dt = 1.0;  // unused in ground mode
+  p.chi_max = dp->chi_max;
+  p.w_max = dp->w_max;
+  p.eps = dp->eps;
+  p.krylov_max = dp->krylov_max;
+  p.krylov_tol = dp->krylov_tol;
+  p.precision = dp->precision;
+  check_params(S, M, &p);
+  ensure_small_buffers(S);
+  const int64_t l0 = g_launches;
+  if (S->env_id != M->id) build_all_envs(S, M, s);
+  tdvp_step_stats st{};
+  double e = 0.0;
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    for (int j = 0; j < S->N - 1; ++j) run_fwd2(S, M, {StageOp{j, 0, 1}}, &p, &st, s, true, &e);
+    for (int j = S->N - 2; j >= 0; --j) run_fwd2(S, M, {StageOp{j, 0, 2}}, &p, &st, s, true, &e);
+  }
+  read_stage_results(S, 0, s);
+  if (ds) {
+    ds->energy = e;
+    ds->w_total = st.w_total;
+    ds->chi_max_seen = st.chi_max_seen;
+    ds->krylov_vectors = st.krylov_vectors;
+    ds->n_updates = st.n_fwd2;
+    ds->kernel_launches = g_launches - l0;
   }
 }
 
@@ -864,6 +910,15 @@ int tdvp_step(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_
     if (!mps || !mpo) fail(TDVP_EINVAL, "NULL handle");
     if (n_steps < 0) fail(TDVP_EINVAL, "n_steps < 0");
     step_impl(mps, mpo, params, n_steps, stats, (cudaStream_t)stream);
+  });
+}
+
+int tdvp_dmrg(tdvp_mps mps, tdvp_mpo mpo, const tdvp_dmrg_params* params, int n_sweeps, tdvp_dmrg_stats* stats,
+              void* stream) {
+  return ok_or_code([&] {
+    if (!mps || !mpo) fail(TDVP_EINVAL, "NULL handle");
+    if (n_sweeps < 0) fail(TDVP_EINVAL, "n_sweeps < 0");
+    dmrg_impl(mps, mpo, params, n_sweeps, stats, (cudaStream_t)stream);
   });
 }
 

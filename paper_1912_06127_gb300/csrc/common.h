@@ -256,6 +256,8 @@ struct LzState {
   int done;      // 1 = converged / breakdown / zero vector
   int kmax;
   int nvec_used;
+  int ground;    // 1: lowest eigenvector instead of the exponential
+  double energy; // ground mode: the Ritz value
 };
 
 // ---------------------------------------------------------------------------

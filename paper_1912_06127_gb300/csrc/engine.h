@@ -84,7 +84,7 @@ void matvec_batch(const std::vector<MvProb>& P, const std::vector<const double2*
                   const std::vector<double2*>& y, const Ctx& c);
 void expm_batch(const std::vector<MvProb>& P, const std::vector<const double2*>& x,
                 const std::vector<double2*>& y, const std::vector<double>& t, int kmax, double tol,
-                const Ctx& c);
+                const Ctx& c, bool ground = false);
 // Environment updates. Left: out [B][m][B] from env [A][m][A], Amat [A][d][B] (= Psi V).
 // Right: out [A][m][A] from env [B][m][B], Bmat [A][d][B] (= V Psi).
 struct EnvProb {

@@ -1,5 +1,6 @@
 // Lanczos exponentiation exp(-i t H) x (Park and Light), batched over the
-// local problems of a stage. Only products H v are needed (Sec. III A), which
+// local problems of a stage; in ground mode the lowest Ritz vector instead
+// (the two-site DMRG update). Only products H v are needed (Sec. III A), which
 // the caller provides as batched launches between the steps below.
 //
 // Per Krylov vector j (all problems of the batch at once, each with its own
@@ -100,6 +101,8 @@ __global__ void __launch_bounds__(LZ_THREADS) lz_start_norm(const __grid_constan
     st->t = P.t;
     st->tol = P.tol;
     st->kmax = P.kmax;
+    st->ground = P.ground;
+    st->energy = 0.0;
     st->k = 0;
     st->err = 0;
     st->nvec_used = 0;
@@ -204,7 +207,15 @@ __global__ void __launch_bounds__(LZ_THREADS) lz_update(const __grid_constant__ 
     const double bnorm = sqrt(s);
     st->alpha[j] = st->h[j].x + st->g[j].x;
     const int k = j + 1;
-    int rc = tridiag_expm_e0_impl(k, st->alpha, st->beta, st->t, st->c, work);
+    int rc;
+    if (st->ground) {
+      // lowest Ritz pair; the estimate below is then the residual beta_{j+1} |z_j|
+      double e0 = 0.0;
+      rc = tridiag_ground_impl(k, st->alpha, st->beta, st->c, &e0, work);
+      st->energy = e0;
+    } else {
+      rc = tridiag_expm_e0_impl(k, st->alpha, st->beta, st->t, st->c, work);
+    }
     if (rc < 0) atomicOr(B.status, 4);
     const double2 ck = st->c[j];
     st->err = bnorm * sqrt(ck.x * ck.x + ck.y * ck.y);

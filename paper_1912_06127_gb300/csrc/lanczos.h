@@ -15,6 +15,7 @@ struct LzDesc {
   int* counter;       // arrival counter (zero between launches)
   double t, tol;
   int kmax;
+  int ground;         // 1: y = ||x|| times the lowest Ritz vector (t unused)
 };
 struct LzBatch {
   int n;

@@ -350,7 +350,7 @@ void matvec_batch(const std::vector<MvProb>& P, const std::vector<const double2*
 // ---------------------------------------------------------------------------
 void expm_batch(const std::vector<MvProb>& P0, const std::vector<const double2*>& x,
                 const std::vector<double2*>& y, const std::vector<double>& t, int kmax, double tol,
-                const Ctx& c) {
+                const Ctx& c, bool ground) {
   const int n = (int)P0.size();
   if (n == 0) return;
   std::vector<MvProb> P = P0;
@@ -371,6 +371,7 @@ void expm_batch(const std::vector<MvProb>& P0, const std::vector<const double2*>
     d.t = t[i];
     d.tol = tol;
     d.kmax = kmax;
+    d.ground = ground ? 1 : 0;
     P[i].skip = &sl->st->done;
   }
   lz_start(lb, c.s);

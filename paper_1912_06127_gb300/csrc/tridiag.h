@@ -1,7 +1,9 @@
-// Exponential of a small real symmetric tridiagonal matrix applied to e_0:
-// c = exp(-i t T) e_0 = Q exp(-i t Theta) Q^T e_0 with T = Q Theta Q^T.
-// Used by the Lanczos exponentiation (Park and Light), which needs only the
-// k x k tridiagonal projection of H_eff (Sec. III A, Eq. 18 / Eq. 20).
+// Eigen-decomposition T = Q Theta Q^T of a small real symmetric tridiagonal
+// matrix, and from it either c = exp(-i t T) e_0 = Q exp(-i t Theta) Q^T e_0
+// (the Lanczos exponentiation of Park and Light, which needs only the k x k
+// tridiagonal projection of H_eff, Sec. III A, Eq. 18 / Eq. 20) or the
+// eigenvector of the lowest eigenvalue (the Lanczos ground state of the
+// two-site DMRG update).
 //
 // The eigen-decomposition is the implicit symmetric QR iteration with
 // Wilkinson shifts (Golub and Van Loan, "Matrix Computations", Sec. 8.3):
@@ -16,10 +18,10 @@
 
 namespace tdvp {
 
-// work must hold 2*k*k doubles. Returns the number of QR steps, or -1 if the
-// iteration did not converge within its limit.
-__host__ __device__ inline int tridiag_expm_e0_impl(int k, const double* alpha, const double* beta,
-                                                    double t, double2* c, double* work) {
+// work must hold 2*k*k doubles; on return the diagonal of T (first k*k) holds
+// the eigenvalues and Q (next k*k, columns) the eigenvectors. Returns the
+// number of QR steps, or -1 if the iteration did not converge within its limit.
+__host__ __device__ inline int tridiag_eig_impl(int k, const double* alpha, const double* beta, double* work) {
   double* T = work;          // k x k, row-major
   double* Q = work + k * k;  // k x k eigenvectors (columns)
   for (int i = 0; i < k * k; ++i) {
@@ -98,6 +100,16 @@ __host__ __device__ inline int tridiag_expm_e0_impl(int k, const double* alpha, 
     }
     ++steps;
   }
+  return steps;
+}
+
+// c = exp(-i t T) e_0; same return value as tridiag_eig_impl.
+__host__ __device__ inline int tridiag_expm_e0_impl(int k, const double* alpha, const double* beta,
+                                                    double t, double2* c, double* work) {
+  const int steps = tridiag_eig_impl(k, alpha, beta, work);
+  if (steps < 0) return steps;
+  const double* T = work;
+  const double* Q = work + k * k;
   for (int i = 0; i < k; ++i) c[i] = make_double2(0.0, 0.0);
   for (int l = 0; l < k; ++l) {
     double th = T[l * k + l];
@@ -110,6 +122,23 @@ __host__ __device__ inline int tridiag_expm_e0_impl(int k, const double* alpha, 
       c[i].y += q * sn;
     }
   }
+  return steps;
+}
+
+// c = eigenvector of the lowest eigenvalue (real, unit norm, sign fixed by
+// c_0 >= 0), *e0 = that eigenvalue; same return value as tridiag_eig_impl.
+__host__ __device__ inline int tridiag_ground_impl(int k, const double* alpha, const double* beta, double2* c,
+                                                   double* e0, double* work) {
+  const int steps = tridiag_eig_impl(k, alpha, beta, work);
+  if (steps < 0) return steps;
+  const double* T = work;
+  const double* Q = work + k * k;
+  int lmin = 0;
+  for (int l = 1; l < k; ++l)
+    if (T[l * k + l] < T[lmin * k + lmin]) lmin = l;
+  *e0 = T[lmin * k + lmin];
+  const double sg = Q[0 * k + lmin] < 0.0 ? -1.0 : 1.0;
+  for (int i = 0; i < k; ++i) c[i] = make_double2(sg * Q[i * k + lmin], 0.0);
   return steps;
 }
 

@@ -49,6 +49,20 @@ class StepStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class DmrgParams(ctypes.Structure):
+    _fields_ = [("chi_max", ctypes.c_int), ("w_max", ctypes.c_double), ("eps", ctypes.c_double),
+                ("krylov_max", ctypes.c_int), ("krylov_tol", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class DmrgStats(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("w_total", ctypes.c_double), ("chi_max_seen", ctypes.c_int),
+                ("krylov_vectors", ctypes.c_int64), ("n_updates", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -83,6 +97,8 @@ def lib():
         "tdvp_step": ([_P, _P, ctypes.POINTER(StepParams), ctypes.c_int, ctypes.POINTER(StepStats), _P],
                       ctypes.c_int),
         "tdvp_measure": ([_P, ctypes.c_int, _D], ctypes.c_int),
+        "tdvp_dmrg": ([_P, _P, ctypes.POINTER(DmrgParams), ctypes.c_int, ctypes.POINTER(DmrgStats), _P],
+                      ctypes.c_int),
         "tdvp_norm": ([_P, _D], ctypes.c_int),
         "tdvp_energy": ([_P, _P, _D], ctypes.c_int),
         "tdvp_overlap": ([_P, _P, _D], ctypes.c_int),
@@ -265,6 +281,18 @@ def step(mps: Mps, mpo: Mpo, params: StepParams, n_steps: int = 1, stream=None,
          stats: Optional[StepStats] = None) -> StepStats:
     st = stats if stats is not None else StepStats()
     _check(lib().tdvp_step(mps.handle, mpo.handle, ctypes.byref(params), n_steps, ctypes.byref(st),
+                           _stream(stream)))
+    return st
+
+
+def dmrg_params(chi_max: int, w_max: float = 0.0, eps: float = 1e-12, krylov_max: int = 8,
+                krylov_tol: float = 1e-6, precision: int = FP64) -> DmrgParams:
+    return DmrgParams(chi_max, w_max, eps, krylov_max, krylov_tol, precision)
+
+
+def dmrg(mps: Mps, mpo: Mpo, params: DmrgParams, n_sweeps: int = 1, stream=None) -> DmrgStats:
+    st = DmrgStats()
+    _check(lib().tdvp_dmrg(mps.handle, mpo.handle, ctypes.byref(params), n_sweeps, ctypes.byref(st),
                            _stream(stream)))
     return st
 
