@@ -966,11 +966,12 @@ ZGemmDesc gemm(int M, int N, int K, const double2* A, int64_t ars, int64_t acs, 
   return q;
 }
 
+// measurement products in double-float (~1e-14 relative, on the FP32 pipe)
 void run1(const ZGemmDesc& q, cudaStream_t s) {
   ZGemmBatch g{};
   g.n = 1;
   g.d[0] = q;
-  launch_zgemm(g, s);
+  launch_zgemm_dd(g, s, "measure_dd");
 }
 
 struct MeasureBufs {
@@ -1017,7 +1018,7 @@ void measure_impl(tdvp_mps_s* S, const double2 op[4], double* out, bool want_loc
   mb.Mj = dalloc<double2>(big);
   mb.X = dalloc<double2>(big);
   mb.Y = dalloc<double2>(big);
-  mb.rho = dalloc<double2>(16);
+  mb.rho = dalloc<double2>((size_t)16 * N);
   mb.EL.resize(N + 1);
   for (int j = 0; j <= N; ++j) {
     const int c = j == 0 ? 1 : S->chiR(j - 1);
@@ -1049,17 +1050,19 @@ void measure_impl(tdvp_mps_s* S, const double2 op[4], double* out, bool want_loc
     // E'[a][a'] = sum_(s b) conj(M[a][(s b)]) Y[a'][(s b)]
     run1(gemm(A, A, d * B, mb.Mj, (int64_t)d * B, 1, 1, mb.Y, 1, (int64_t)d * B, mb.ER[j - 1], A), s);
   }
-  std::vector<double2> rho(d * d);
   for (int j = 0; j < N; ++j) {
     site_matrix(S, j, mb.Mj, s);
     const int A = S->chiL(j), B = S->chiR(j);
     run1(gemm(A, d * B, A, mb.EL[j], A, 1, 0, mb.Mj, (int64_t)d * B, 1, mb.X, (int64_t)d * B), s);
     run1(gemm(A * d, B, B, mb.X, B, 1, 0, mb.ER[j], 1, B, mb.Y, B), s);
-    rho_kernel<<<d * d, 256, 0, s>>>(mb.Mj, mb.Y, A, d, B, mb.rho);
+    rho_kernel<<<d * d, 256, 0, s>>>(mb.Mj, mb.Y, A, d, B, mb.rho + (size_t)16 * j);
     LAUNCH_CHECK();
-    CUDA_TRY(cudaMemcpy(rho.data(), mb.rho, sizeof(double2) * d * d, cudaMemcpyDeviceToHost));
+  }
+  std::vector<double2> rho((size_t)16 * N);
+  CUDA_TRY(cudaMemcpy(rho.data(), mb.rho, sizeof(double2) * 16 * N, cudaMemcpyDeviceToHost));
+  for (int j = 0; j < N; ++j) {
     double v = 0;
-    for (int q = 0; q < d * d; ++q) v += rho[q].x * op[q].x - rho[q].y * op[q].y;
+    for (int q = 0; q < d * d; ++q) v += rho[16 * j + q].x * op[q].x - rho[16 * j + q].y * op[q].y;
     out[j] = v / nrm.x;
   }
 }

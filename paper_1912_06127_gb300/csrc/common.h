@@ -119,7 +119,7 @@ constexpr int KRYLOV_MAX = 24;  // largest Krylov dimension
 struct ZGemmDesc {
   int M, N, K;
   int conj_a, conj_b, accumulate;
-  int upper_only;         // only output tiles on or above the diagonal (Hermitian results)
+  int upper_only;         // only output blocks of 64 x 64 on or above the diagonal (Hermitian results)
   const int* skip;        // optional: nonzero -> problem skipped
   const double2* A;
   const double2* B;

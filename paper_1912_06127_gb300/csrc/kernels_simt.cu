@@ -135,39 +135,42 @@ void launch_zgemm(const ZGemmBatch& b, cudaStream_t s, const char* prof_name) {
 // (hi, lo) pairs when staged in shared memory, each product's leading term
 // exact through FMA and accumulated with two_sum, the small terms in FP32.
 // ---------------------------------------------------------------------------
+template <int TT>  // outputs per thread along each side: tile (16 TT) x (16 TT)
 __global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ ZGemmBatch batch) {
+  constexpr int BM = 16 * TT, BN = 16 * TT;
   const int pid = blockIdx.y;
   if (pid >= batch.n) return;
   const ZGemmDesc& P = batch.d[pid];
   if (P.skip && *P.skip) return;
-  const int tiles_m = (P.M + ZG_BM - 1) / ZG_BM;
-  const int tiles_n = (P.N + ZG_BN - 1) / ZG_BN;
+  const int tiles_m = (P.M + BM - 1) / BM;
+  const int tiles_n = (P.N + BN - 1) / BN;
   if ((int)blockIdx.x >= tiles_m * tiles_n) return;
   const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
-  if (P.upper_only && tm > tn) return;
-  const int m0 = tm * ZG_BM, n0 = tn * ZG_BN;
-  __shared__ float4 As[ZG_BK][ZG_BM];  // (re_hi, im_hi, re_lo, im_lo)
-  __shared__ float4 Bs[ZG_BK][ZG_BN];
+  const int m0 = tm * BM, n0 = tn * BN;
+  // Hermitian results: the blocks of 64 on or above the diagonal (any tile size)
+  if (P.upper_only && m0 / 64 > n0 / 64) return;
+  __shared__ float4 As[ZG_BK][BM];  // (re_hi, im_hi, re_lo, im_lo)
+  __shared__ float4 Bs[ZG_BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  float sr[4][4], cr[4][4], si[4][4], ci[4][4];
+  float sr[TT][TT], cr[TT][TT], si[TT][TT], ci[TT][TT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sr[i][j] = cr[i][j] = si[i][j] = ci[i][j] = 0.f;
+    for (int j = 0; j < TT; ++j) sr[i][j] = cr[i][j] = si[i][j] = ci[i][j] = 0.f;
   const bool a_k_fast = (P.a_cs == 1);
   const bool b_n_fast = (P.b_cs == 1);
   for (int k0 = 0; k0 < P.K; k0 += ZG_BK) {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < (ZG_BK * BM) / 256; ++r) {
       int e = tid + r * 256;
       int i, k;
       if (a_k_fast) {
         k = e % ZG_BK;
         i = e / ZG_BK;
       } else {
-        i = e % ZG_BM;
-        k = e / ZG_BM;
+        i = e % BM;
+        k = e / BM;
       }
       double2 v = make_double2(0.0, 0.0);
       int gi = m0 + i, gk = k0 + k;
@@ -186,8 +189,8 @@ __global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ Z
       }
       int j, kb;
       if (b_n_fast) {
-        j = e % ZG_BN;
-        kb = e / ZG_BN;
+        j = e % BN;
+        kb = e / BN;
       } else {
         kb = e % ZG_BK;
         j = e / ZG_BK;
@@ -206,15 +209,15 @@ __global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ Z
     __syncthreads();
 #pragma unroll 2
     for (int kk = 0; kk < ZG_BK; ++kk) {
-      float4 a[4], b[4];
+      float4 a[TT], b[TT];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TT; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TT; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TT; ++j) {
           // re += a.re b.re - a.im b.im ; im += a.re b.im + a.im b.re
           dd_acc(sr[i][j], cr[i][j], a[i].x, a[i].z, b[j].x, b[j].z);
           dd_acc(sr[i][j], cr[i][j], -a[i].y, -a[i].w, b[j].y, b[j].w);
@@ -225,11 +228,11 @@ __global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ Z
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TT; ++i) {
     int gi = m0 + ty + 16 * i;
     if (gi >= P.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TT; ++j) {
       int gj = n0 + tx + 16 * j;
       if (gj >= P.N) continue;
       double2* c = P.C + (int64_t)gi * P.c_rs + (int64_t)gj * P.c_cs;
@@ -242,11 +245,16 @@ __global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ Z
 
 void launch_zgemm_dd(const ZGemmBatch& b, cudaStream_t s, const char* prof_name) {
   if (b.n <= 0) return;
+  // 64 x 64 tiles when the batch fills the GPU, else 32 x 32 (4x the CTAs)
+  int64_t tiles64 = 0;
+  for (int i = 0; i < b.n; ++i) tiles64 += (int64_t)cdiv(b.d[i].M, 64) * cdiv(b.d[i].N, 64);
+  const int tt = tiles64 >= 2 * 152 ? 4 : 2;
+  const int bm = 16 * tt;
   int maxt = 0;
   for (int i = 0; i < b.n; ++i) {
     const auto& d = b.d[i];
     if (d.M <= 0 || d.N <= 0) continue;
-    maxt = std::max(maxt, cdiv(d.M, ZG_BM) * cdiv(d.N, ZG_BN));
+    maxt = std::max(maxt, cdiv(d.M, bm) * cdiv(d.N, bm));
   }
   if (maxt == 0) return;
   double fl = 0, by = 0;
@@ -257,7 +265,8 @@ void launch_zgemm_dd(const ZGemmBatch& b, cudaStream_t s, const char* prof_name)
   }
   ProfScope ps(prof_name, s, fl, by);
   dim3 grid(maxt, b.n);
-  zgemm_dd_kernel<<<grid, 256, 0, s>>>(b);
+  if (tt == 4) zgemm_dd_kernel<4><<<grid, 256, 0, s>>>(b);
+  else zgemm_dd_kernel<2><<<grid, 256, 0, s>>>(b);
   LAUNCH_CHECK();
   ++g_launches;
 }
