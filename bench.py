@@ -57,8 +57,9 @@ def parse():
     return ap.parse_args()
 
 
-def svd_case(n):
-    """The split of one evolved two-site state (Fig. 5) at chi = n / 2: a seeded
+def svd_case(n, prec):
+    """The split of one evolved two-site state (Fig. 5) at chi = n / 2, with
+    the SVD of the path of precision `prec` (--precision): a seeded
     n x n matrix whose singular values fall from 1 to 6.5e-3 over the first
     half (the previous bond's Schmidt values) and from 7e-4 to 4e-6 over the
     second (the weight one time step moves into new directions), truncated to
@@ -74,11 +75,11 @@ def svd_case(n):
         PsiL = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
         PsiR = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
         V = torch.zeros(n, dtype=torch.float64, device="cuda")
-        chi, w = tdvp.op_split(n, n, th, n // 2, 0.0, 1e-12, PsiL, V, PsiR, None)
+        chi, w = tdvp.op_split(n, n, th, n // 2, 0.0, 1e-12, PsiL, V, PsiR, None, precision=prec)
         torch.cuda.synchronize()
     w_ref = float((s[n // 2:] ** 2).sum())
     print(json.dumps({"svd_case": n, "chi": chi, "w": w, "w_expected": w_ref}))
-    if chi != n // 2 or abs(w - w_ref) > 1e-9 * w_ref:
+    if chi != n // 2 or abs(w - w_ref) > 1e-9 * float((s ** 2).sum()):
         raise SystemExit("svd case: unexpected truncation")
 
 
@@ -454,7 +455,7 @@ def state_gb(mdl, chi):
 def main():
     args = parse()
     if args.svd_case:
-        svd_case(args.svd_case)
+        svd_case(args.svd_case, PREC[args.precision])
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -265,6 +265,13 @@ int tdvp_op_expm(int precision, int nsite, int chi_l, int chi_r, int m, int d, c
 int tdvp_op_split(int rows, int cols, const double* theta, int chi_max, double w_max, double eps,
                   double* Psi_L, double* V, double* Psi_R, double* s_out, int* chi, double* w,
                   void* stream);
+/* tdvp_op_split with the SVD of a given path: TDVP_FP64 as tdvp_op_split;
+ * TDVP_TF32 / TDVP_TF32X3 the mixed-precision path's SVD (FP32 Jacobi phase,
+ * double-float finishing sweeps to ~1e-10 relative orthogonality, FP32
+ * block-rotation updates of the unitary factor), as used by tdvp_step. */
+int tdvp_op_split_prec(int precision, int rows, int cols, const double* theta, int chi_max, double w_max,
+                       double eps, double* Psi_L, double* V, double* Psi_R, double* s_out, int* chi,
+                       double* w, void* stream);
 
 /* Same as tdvp_op_heff with precision TDVP_FP64, for callers that cannot
  * allocate device memory (a stream capture that forbids allocation, a host

@@ -1310,7 +1310,14 @@ int tdvp_op_env(int precision, int side, int chi_l, int chi_r, int m, int d, con
 
 int tdvp_op_split(int rows, int cols, const double* theta, int chi_max, double w_max, double eps, double* Psi_L,
                   double* V, double* Psi_R, double* s_out, int* chi, double* w, void* stream) {
+  return tdvp_op_split_prec(TDVP_FP64, rows, cols, theta, chi_max, w_max, eps, Psi_L, V, Psi_R, s_out, chi, w,
+                            stream);
+}
+
+int tdvp_op_split_prec(int precision, int rows, int cols, const double* theta, int chi_max, double w_max, double eps,
+                       double* Psi_L, double* V, double* Psi_R, double* s_out, int* chi, double* w, void* stream) {
   return ok_or_code([&] {
+    if (precision < TDVP_FP64 || precision > TDVP_TF32X3) fail(TDVP_EINVAL, "invalid precision");
     if (!theta || !Psi_L || !V || !Psi_R || !chi || !w) fail(TDVP_EINVAL, "NULL argument");
     if (rows < 1 || cols < 1 || rows > 4096 || cols > 4096 || chi_max < 1 || w_max < 0 || eps < 0)
       fail(TDVP_EINVAL, "invalid arguments");
@@ -1322,6 +1329,7 @@ int tdvp_op_split(int rows, int cols, const double* theta, int chi_max, double w
     // the Acc buffer must hold nv*nv and X nv*len: both <= cap_vec = max(nv*len, nv*nv)
     SvdBatch sb{};
     sb.n = 1;
+    sb.mode = precision == TDVP_FP64 ? 0 : 1;
     sb.status = C.d_status;
     sb.sync = C.slot.sync;
     SvdDesc& q = sb.d[0];

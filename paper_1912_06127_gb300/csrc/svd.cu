@@ -1473,8 +1473,9 @@ void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
     else { x.b_rs = 1; x.b_cs = P.cols; }
     x.C = P.X; x.c_rs = P.len; x.c_cs = 1;
   }
-  // Newton-Schulz steps: unitarity error ~1e-5 (FP32 rotations) -> ~1e-10 -> ~1e-16
-  const int ns_steps = b.mode == 0 ? 2 : 1;
+  // Newton-Schulz steps: the FP32 rotation's unitarity defect (up to ~1e-4
+  // after many sweeps) -> ~1e-8 -> rounding, on both paths
+  const int ns_steps = 2;
   for (int it = 0; it < ns_steps; ++it) {
     if (b.mode == 1) launch_zgemm_dd(gp, s, "svd_newton_schulz_dd");
     else launch_zgemm(gp, s, "svd_newton_schulz");

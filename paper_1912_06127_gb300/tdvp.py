@@ -108,6 +108,8 @@ def lib():
                                                ctypes.c_double, _I, _P], ctypes.c_int),
         "tdvp_op_split": ([ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                            _P, _P, _P, _P, _I, _D, _P], ctypes.c_int),
+        "tdvp_op_split_prec": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                           _P, _P, _P, _P, _I, _D, _P], ctypes.c_int),
         "tdvp_schedule": ([ctypes.c_int, ctypes.c_int, _I, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int],
                           ctypes.c_int),
         "tdvp_tridiag_expm": ([ctypes.c_int, _D, _D, ctypes.c_double, _D], ctypes.c_int),
@@ -350,12 +352,12 @@ def op_expm(precision, nsite, chi_l, chi_r, m, d, W, L, R, x, y, t, kmax, tol, s
     return nv.value
 
 
-def op_split(rows, cols, theta, chi_max, w_max, eps, Psi_L, V, Psi_R, s_out=None, stream=None):
+def op_split(rows, cols, theta, chi_max, w_max, eps, Psi_L, V, Psi_R, s_out=None, stream=None, precision=FP64):
     chi = ctypes.c_int(0)
     w = ctypes.c_double(0)
-    _check(lib().tdvp_op_split(rows, cols, _ptr(theta), chi_max, w_max, eps, _ptr(Psi_L), _ptr(V), _ptr(Psi_R),
-                               _ptr(s_out) if s_out is not None else None, ctypes.byref(chi), ctypes.byref(w),
-                               _stream(stream)))
+    _check(lib().tdvp_op_split_prec(precision, rows, cols, _ptr(theta), chi_max, w_max, eps, _ptr(Psi_L), _ptr(V),
+                                    _ptr(Psi_R), _ptr(s_out) if s_out is not None else None, ctypes.byref(chi),
+                                    ctypes.byref(w), _stream(stream)))
     return chi.value, w.value
 
 

@@ -261,6 +261,38 @@ def test_split_tail_rule(n, chi_max, w_max, deg):
     assert np.abs(outs[0] - outs[1]).max() < 1e-12
 
 
+@pytest.mark.parametrize("n,chi_max", [(160, 80), (512, 256)])
+def test_split_mixed_precision_path(n, chi_max):
+    """The mixed path's SVD (FP32 sweeps, double-float finishing sweeps, FP32
+    block-rotation updates of the unitary factor) at the full bond size of the
+    benchmark: kept values, isometries and the truncated product to the ~1e-8
+    its orthogonality target allows."""
+    torch = torch_or_skip()
+    tdvp = lib()
+    theta, _ = gapped_matrix(n, n // 2, 95)
+    s_ref = np.linalg.svd(theta, compute_uv=False)
+    chi_ref, w_ref = T.truncation_rank(s_ref, chi_max, 0.0, 1e-12)
+    PsiL = torch.zeros(n * n, dtype=torch.complex128, device="cuda")
+    PsiR = torch.zeros(n * n, dtype=torch.complex128, device="cuda")
+    V = torch.zeros(n, dtype=torch.float64, device="cuda")
+    chi, w = tdvp.op_split(n, n, dev(torch, theta), chi_max, 0.0, 1e-12, PsiL, V, PsiR, None, precision=TF32X3)
+    assert chi == chi_ref
+    # w is a small remainder of ||theta||^2: its error is set by the unitarity
+    # of the transformed vectors (~1e-10 here), relative to ||theta||^2
+    assert abs(w - w_ref) <= 1e-10 * np.sum(s_ref ** 2)
+    v = V.cpu().numpy()[:chi]
+    assert np.allclose(1.0 / v, s_ref[:chi], rtol=1e-7, atol=1e-10 * s_ref[0])
+    pl = host(PsiL)[: n * chi].reshape(n, chi)
+    pr = host(PsiR)[: chi * n].reshape(chi, n)
+    A = pl * v[None, :]
+    B = v[:, None] * pr
+    assert np.abs(A.conj().T @ A - np.eye(chi)).max() < 1e-7
+    assert np.abs(B @ B.conj().T - np.eye(chi)).max() < 1e-7
+    U, sv, Vh = np.linalg.svd(theta)
+    best = (U[:, :chi] * sv[:chi]) @ Vh[:chi]
+    assert np.abs((pl * v[None, :]) @ pr - best).max() < 1e-7 * s_ref[0]
+
+
 @pytest.mark.parametrize("prec", [FP64, TF32X3], ids=["fp64", "tf32x3"])
 def test_heff_full_size_sampled(prec):
     """H_eff at the chi = 256, m = 10 (N = 101 Ising, 8 exponentials) size of the
