@@ -603,9 +603,12 @@ template <typename T>
 struct RotRec {
   typename Prec<T>::R cs;
   typename Prec<T>::CT m1, m2;  // identity rotation: cs = 1, m1 = m2 = 0
-  // FP32 copies for the accumulation of the block rotation in FP32 (cm1 = cs - 1)
+  // FP32 copies for the accumulation of the block rotation in FP32 (cm1 = cs - 1),
+  // and the low parts that make (cm1, m1, m2) double-float
   float cm1;
   float2 m1f, m2f;
+  float cm1l;
+  float2 m1l, m2l;
 };
 
 template <typename T, int W>
@@ -728,6 +731,12 @@ __device__ inline void dd_axpy3(float xh, float xl, float p1h, float p1l, float 
   fast_two_sum(s, c, oh, ol);
 }
 
+template <typename T>
+struct RotOut {
+  RotRec<T> rec;
+  int rot;
+};
+
 // One local round: warp w rotates local vectors (lp, lq); every thread of the
 // CTA calls it (it ends with a barrier).
 template <typename T, int W>
@@ -748,51 +757,74 @@ __device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec
   if (active) block_cross<T, W>(x, y, lane, kr, ki);
   RotRec<T> rec;
   int rot = 0;
-  if (lane == 0) {
-    rec.cs = 1;
-    rec.m1 = rec.m2 = Prec<T>::mkc(0, 0);
-    rec.cm1 = 0.f;
-    rec.m1f = rec.m2f = make_float2(0.f, 0.f);
-    if (active) {
-      const R a = nrm[lp], b = nrm[lq];
+  // the parameters of one pair: lane `who` of the calling warp, with (lp, lq), kr, ki
+  auto params = [&](int plp, int plq, R pkr, R pki, bool pact) {
+    RotRec<T> r;
+    r.cs = 1;
+    r.m1 = r.m2 = Prec<T>::mkc(0, 0);
+    r.cm1 = r.cm1l = 0.f;
+    r.m1f = r.m2f = r.m1l = r.m2l = make_float2(0.f, 0.f);
+    int did = 0;
+    if (pact) {
+      const R a = nrm[plp], b = nrm[plq];
       R a2, b2;
       float ratio = 0.f;
       atomicAdd(n_rot + 1, 1);  // pairs checked
-      if (jacobi_rotation_fast<T>(tol2, zl, a, b, kr, ki, rec, a2, b2, ratio)) {
-        rot = 1;
-        rec.cm1 = (float)(rec.cs - R(1));
-        rec.m1f = make_float2((float)rec.m1.x, (float)rec.m1.y);
-        rec.m2f = make_float2((float)rec.m2.x, (float)rec.m2.y);
-        nrm[lp] = a2;
-        nrm[lq] = b2;
+      if (jacobi_rotation_fast<T>(tol2, zl, a, b, pkr, pki, r, a2, b2, ratio)) {
+        did = 1;
+        r.cm1 = (float)(r.cs - R(1));
+        r.m1f = make_float2((float)r.m1.x, (float)r.m1.y);
+        r.m2f = make_float2((float)r.m2.x, (float)r.m2.y);
+        if constexpr (Prec<T>::dd) {
+          r.cm1l = (float)((double)(r.cs - R(1)) - (double)r.cm1);
+          r.m1l = make_float2((float)((double)r.m1.x - (double)r.m1f.x), (float)((double)r.m1.y - (double)r.m1f.y));
+          r.m2l = make_float2((float)((double)r.m2.x - (double)r.m2f.x), (float)((double)r.m2.y - (double)r.m2f.y));
+        }
+        nrm[plp] = a2;
+        nrm[plq] = b2;
         atomicAdd(n_rot, 1);
         atomicMax(maxr_bits, __float_as_uint(ratio));
       }
     }
-    seq[slot] = rec;
+    return RotOut<T>{r, did};
+  };
+  if constexpr (std::is_same<R, double>::value) {
+    // FP64 parameters (a few dozen FP64 instructions, each occupying the FP64
+    // pipe for a whole warp): one warp computes those of all W pairs of the
+    // round, its lanes in parallel, instead of one lane in every warp
+    __shared__ double2 pk[W];
+    __shared__ int ppq[W], prot[W];
+    const int warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      pk[warp] = make_double2((double)kr, (double)ki);
+      ppq[warp] = active ? (lp | (lq << 8)) : -1;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < W) {
+      const int pq = ppq[lane];
+      const auto res = params(pq & 255, (pq >> 8) & 255, (R)pk[lane].x, (R)pk[lane].y, pq >= 0);
+      seq[slot - warp + lane] = res.rec;
+      prot[lane] = res.rot;
+    }
+    __syncthreads();
+    rot = prot[warp];
+    if (rot) rec = seq[slot];
+  } else {
+    if (lane == 0) {
+      const auto res = params(lp, lq, kr, ki, active);
+      rec = res.rec;
+      rot = res.rot;
+      seq[slot] = rec;
+    }
   }
   rot = __shfl_sync(0xffffffffu, rot, 0);
   if (rot) {
     if constexpr (Prec<T>::dd) {
-      // x' = x + [(cs - 1) x + m1 y], y' = y + [(cs - 1) y + m2 x] in double-float
-      float2 c1 = make_float2(0.f, 0.f), a1 = c1, b1 = c1, a2 = c1, b2 = c1;  // hi/lo of cs-1, m1, m2
-      if (lane == 0) {
-        c1 = dd_split(rec.cs - 1.0);
-        a1 = dd_split(rec.m1.x);
-        b1 = dd_split(rec.m1.y);
-        a2 = dd_split(rec.m2.x);
-        b2 = dd_split(rec.m2.y);
-      }
-      c1.x = __shfl_sync(0xffffffffu, c1.x, 0);
-      c1.y = __shfl_sync(0xffffffffu, c1.y, 0);
-      a1.x = __shfl_sync(0xffffffffu, a1.x, 0);
-      a1.y = __shfl_sync(0xffffffffu, a1.y, 0);
-      b1.x = __shfl_sync(0xffffffffu, b1.x, 0);
-      b1.y = __shfl_sync(0xffffffffu, b1.y, 0);
-      a2.x = __shfl_sync(0xffffffffu, a2.x, 0);
-      a2.y = __shfl_sync(0xffffffffu, a2.y, 0);
-      b2.x = __shfl_sync(0xffffffffu, b2.x, 0);
-      b2.y = __shfl_sync(0xffffffffu, b2.y, 0);
+      // x' = x + [(cs - 1) x + m1 y], y' = y + [(cs - 1) y + m2 x] in double-float;
+      // every lane holds the record (read from shared memory)
+      const float2 c1 = make_float2(rec.cm1, rec.cm1l);
+      const float2 a1 = make_float2(rec.m1f.x, rec.m1l.x), b1 = make_float2(rec.m1f.y, rec.m1l.y);
+      const float2 a2 = make_float2(rec.m2f.x, rec.m2l.x), b2 = make_float2(rec.m2f.y, rec.m2l.y);
 #pragma unroll 2
       for (int i = 0; i < C::EPT; ++i) {
         const float4 u = x[lane + 32 * i], v = y[lane + 32 * i];
@@ -847,7 +879,7 @@ __device__ inline void block_replay_acc(const SvdDesc& P, const int* vrows, cons
           int p = 0, q = 0;
           rr_pair(W, rr, w % (W / 2), p, q);
           const int o = w < W / 2 ? 0 : W;
-          const RotRec<T> rec = seq[rr * W + w];
+          const RotRec<T>& rec = seq[rr * W + w];
           apply_rot<T>(acc[p + o], acc[q + o], rec);
         }
       }
@@ -858,7 +890,7 @@ __device__ inline void block_replay_acc(const SvdDesc& P, const int* vrows, cons
       for (int rr = 0; rr < W; ++rr) {
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-          const RotRec<T> rec = seq[base + rr * W + w];
+          const RotRec<T>& rec = seq[base + rr * W + w];
           apply_rot<T>(acc[w], acc[W + (w + rr) % W], rec);
         }
       }
