@@ -201,8 +201,17 @@ def fp64_peak_tflops():
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
-def roofline(prof, steps, clk=None, kernel=None):
-    """Roofline entry for `kernel` (default: the kind with the largest device time)."""
+# DRAM bytes (read + write) per local problem of the Jacobi kernels, from one ncu
+# capture of a 512 x 512 split (profiles/svd_block_sweeps_split512.md); a launch
+# of the time step carries several problems, and its traffic scales with them
+# (each problem's vectors and rotation are read once and written once; the
+# sweeps run in L2). None once a kernel changes after the capture.
+TRAFFIC_PER_PROBLEM = {"svd_jacobi_fp32": 4.805888e6 + 4.152320e6, "svd_jacobi_dd": 8.535808e6 + 0.729088e6}
+
+
+def roofline(prof, steps, clk=None, kernel=None, problems=None):
+    """Roofline entry for `kernel` (default: the kind with the largest device time);
+    `problems`: local problems (two-site updates) in the timed region."""
     if not prof:
         return None, None
     dom = kernel if kernel in prof else max(prof, key=lambda k: prof[k]["ms"])
@@ -242,6 +251,10 @@ def roofline(prof, steps, clk=None, kernel=None):
     r["ms_per_launch"] = ms_launch
     r["launches"] = d["launches"]
     r["traffic"] = None
+    if dom in TRAFFIC_PER_PROBLEM and problems:
+        r["traffic"] = TRAFFIC_PER_PROBLEM[dom] * problems / d["launches"]
+        r["traffic_source"] = ("ncu dram__bytes_read+write of one 512x512 split, x %.1f problems per launch"
+                               % (problems / d["launches"]))
     return r, dom
 
 
@@ -375,7 +388,7 @@ def run_ours(args, world, rank, local):
     if rank != 0:
         return
     value = job_value(args.steps, ms_max, world)
-    rl, dom = roofline(prof, args.steps, clk)
+    rl, dom = roofline(prof, args.steps, clk, problems=st.n_fwd2)
     tc_kind = "tc_gemm_tf32x3" if args.precision == "tf32x3" else "tc_gemm_tf32"
     rl_heff, _ = roofline(prof, args.steps, clk, tc_kind) if tc_kind in prof else (None, None)
     heff_ms = sum(v["ms"] for k, v in prof.items() if k.startswith("tc_gemm") or k == "zgemm_fp64"
