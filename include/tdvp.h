@@ -158,6 +158,15 @@ int tdvp_init_mps(int N, int d, const int* basis_state, int chi_cap, tdvp_mps* o
  * chi_cap and to singular values > eps * lambda_1, and normalises it. */
 int tdvp_init_mps_tensors(int N, int d, const int* dims, const double* const* tensors,
                           int chi_cap, double eps, tdvp_mps* out);
+/* Bring `mps` back to the inverse canonical gauge (Sec. II B) and unit norm:
+ * a left-to-right then right-to-left SVD sweep over Psi_1 V_1 Psi_2 ... Psi_N
+ * (bond dimensions capped at the handle's chi_cap, singular values below
+ * eps * lambda_1 dropped). The segment scheme breaks the gauge conditions at
+ * segment boundaries; the paper reorthonormalises (and recomputes the
+ * environments) when the error in the norm grows (Sec. III D, Fig. 8). The
+ * environments are rebuilt by the next tdvp_step / tdvp_dmrg. Synchronises the
+ * device. */
+int tdvp_reorthonormalize(tdvp_mps mps, double eps);
 /* Current bond dimensions (N-1 ints). */
 int tdvp_mps_bond_dims(tdvp_mps mps, int* dims_out);
 /* Copy Psi_j (2*chi_l*d*chi_r doubles) or V_j (chi_j doubles) to the host. */

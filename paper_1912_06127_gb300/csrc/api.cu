@@ -651,6 +651,106 @@ int device_split(tdvp_mps_s* S, Slot* sl, const double2* theta, int rows, int co
 
 }  // namespace
 
+// Brings the MPS with raw site tensors raw[j] ([rd[j]][d][rd[j+1]], device,
+// each with room for d * chi_cap * max(rd[j+1], chi_cap) elements) to the
+// inverse canonical gauge of Sec. II B in S: a left-to-right SVD sweep (A_j = U,
+// Lambda V^dagger carried right), normalisation, then a right-to-left sweep
+// (Psi_j = Lambda V^dagger, V_{j-1} = 1 / Lambda), truncating at chi_cap and
+// the relative cutoff eps. Consumes raw. Synchronises s.
+void canonicalize_device(tdvp_mps_s* S, std::vector<double2*>& raw, std::vector<int> rd, int chi_cap, double eps,
+                         cudaStream_t s) {
+  const int N = S->N, d = S->d;
+  int64_t big = 1;
+  for (int j = 0; j < N; ++j) big = std::max<int64_t>(big, (int64_t)std::max(rd[j], chi_cap) * d);
+  for (int j = 0; j <= N; ++j) big = std::max<int64_t>(big, rd[j]);
+  auto* sl = new Slot();
+  std::unique_ptr<Slot> guard(sl);
+  sl->ensure(big * big, 1, 0, big, 1);
+  double2* L = dalloc<double2>(big * big);
+  double2* R = dalloc<double2>(big * big);
+  double* Vt = dalloc<double>(big);
+  // left-to-right: A_j = U, carry Lambda V^dagger into site j+1
+  for (int j = 0; j + 1 < N; ++j) {
+    const int a = rd[j], b = rd[j + 1];
+    const int chi = device_split(S, sl, raw[j], a * d, b, chi_cap, 0.0, eps, L, Vt, R, nullptr, nullptr, s);
+    // A_j = Psi_L V  (= U), stored back in raw[j] as [a][d][chi]
+    ScaleBatch sb{};
+    sb.n = 1;
+    sb.d[0] = ScaleDesc{L, raw[j], Vt, a * d, 1, chi, 0};
+    launch_scale_bond(sb, s);
+    // site j+1 <- (Lambda V^dagger) site j+1
+    const int c = rd[j + 2];
+    ZGemmBatch g{};
+    g.n = 1;
+    g.d[0] = ZGemmDesc{};
+    auto& q = g.d[0];
+    q.M = chi;
+    q.N = d * c;
+    q.K = b;
+    q.A = R;
+    q.a_rs = b;
+    q.a_cs = 1;
+    q.B = raw[j + 1];
+    q.b_rs = (int64_t)d * c;
+    q.b_cs = 1;
+    q.C = sl->theta;
+    q.c_rs = (int64_t)d * c;
+    q.c_cs = 1;
+    launch_zgemm(g, s);
+    CUDA_TRY(cudaMemcpyAsync(raw[j + 1], sl->theta, sizeof(double2) * chi * d * c, cudaMemcpyDeviceToDevice, s));
+    rd[j + 1] = chi;
+  }
+  // normalise: the norm is carried by the last tensor
+  {
+    const int64_t n = (int64_t)rd[N - 1] * d;
+    std::vector<double2> h(n);
+    CUDA_TRY(cudaMemcpy(h.data(), raw[N - 1], sizeof(double2) * n, cudaMemcpyDeviceToHost));
+    double nrm = 0;
+    for (auto& v : h) nrm += v.x * v.x + v.y * v.y;
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0)) fail(TDVP_ENUMERIC, "initial state has zero norm");
+    for (auto& v : h) v = zscale(v, 1.0 / nrm);
+    CUDA_TRY(cudaMemcpy(raw[N - 1], h.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
+  }
+  // right-to-left: C = U Lambda V^dagger; Psi_j = Lambda V^dagger, V_{j-1} = 1/Lambda
+  for (int j = N - 1; j >= 1; --j) {
+    const int a = rd[j], c = rd[j + 1];
+    const int chi = device_split(S, sl, raw[j], a, d * c, chi_cap, 0.0, eps, L, S->V[j - 1], S->Psi[j],
+                                 nullptr, nullptr, s);
+    S->dims[j - 1] = chi;
+    // site j-1 <- A_{j-1} (U Lambda)
+    const int p = rd[j - 1];
+    ZGemmBatch g{};
+    g.n = 1;
+    g.d[0] = ZGemmDesc{};
+    auto& q = g.d[0];
+    q.M = p * d;
+    q.N = chi;
+    q.K = a;
+    q.A = raw[j - 1];
+    q.a_rs = a;
+    q.a_cs = 1;
+    q.B = L;
+    q.b_rs = chi;
+    q.b_cs = 1;
+    q.C = sl->theta;
+    q.c_rs = chi;
+    q.c_cs = 1;
+    launch_zgemm(g, s);
+    CUDA_TRY(cudaMemcpyAsync(raw[j - 1], sl->theta, sizeof(double2) * p * d * chi, cudaMemcpyDeviceToDevice, s));
+    rd[j] = chi;
+  }
+  CUDA_TRY(cudaMemcpyAsync(S->Psi[0], raw[0], sizeof(double2) * d * rd[1], cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  dfree(L);
+  dfree(R);
+  dfree(Vt);
+}
+
+namespace {
+void site_matrix(tdvp_mps_s* S, int j, double2* dst, cudaStream_t s);
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -775,98 +875,41 @@ int tdvp_init_mps_tensors(int N, int d, const int* dims, const double* const* te
         raw[j] = dalloc<double2>(std::max<int64_t>(n, (int64_t)d * chi_cap * std::max(dims[j + 1], chi_cap)));
         CUDA_TRY(cudaMemcpy(raw[j], tensors[j], sizeof(double2) * n, cudaMemcpyHostToDevice));
       }
-      std::vector<int> rd(dims, dims + N + 1);  // current raw dims
-      int64_t big = 1;
-      for (int j = 0; j < N; ++j) big = std::max<int64_t>(big, (int64_t)std::max(rd[j], chi_cap) * d);
-      for (int j = 0; j <= N; ++j) big = std::max<int64_t>(big, rd[j]);
-      auto* sl = new Slot();
-      std::unique_ptr<Slot> guard(sl);
-      sl->ensure(big * big, 1, 0, big, 1);
-      double2* L = dalloc<double2>(big * big);
-      double2* R = dalloc<double2>(big * big);
-      double* Vt = dalloc<double>(big);
-      // left-to-right: A_j = U, carry Lambda V^dagger into site j+1
-      for (int j = 0; j + 1 < N; ++j) {
-        const int a = rd[j], b = rd[j + 1];
-        const int chi = device_split(S, sl, raw[j], a * d, b, chi_cap, 0.0, eps, L, Vt, R, nullptr, nullptr, s);
-        // A_j = Psi_L V  (= U), stored back in raw[j] as [a][d][chi]
-        ScaleBatch sb{};
-        sb.n = 1;
-        sb.d[0] = ScaleDesc{L, raw[j], Vt, a * d, 1, chi, 0};
-        launch_scale_bond(sb, s);
-        // site j+1 <- (Lambda V^dagger) site j+1
-        const int c = rd[j + 2];
-        ZGemmBatch g{};
-        g.n = 1;
-        g.d[0] = ZGemmDesc{};
-        auto& q = g.d[0];
-        q.M = chi;
-        q.N = d * c;
-        q.K = b;
-        q.A = R;
-        q.a_rs = b;
-        q.a_cs = 1;
-        q.B = raw[j + 1];
-        q.b_rs = (int64_t)d * c;
-        q.b_cs = 1;
-        q.C = sl->theta;
-        q.c_rs = (int64_t)d * c;
-        q.c_cs = 1;
-        launch_zgemm(g, s);
-        CUDA_TRY(cudaMemcpyAsync(raw[j + 1], sl->theta, sizeof(double2) * chi * d * c, cudaMemcpyDeviceToDevice, s));
-        rd[j + 1] = chi;
-      }
-      // normalise: the norm is carried by the last tensor
-      {
-        const int64_t n = (int64_t)rd[N - 1] * d;
-        std::vector<double2> h(n);
-        CUDA_TRY(cudaMemcpy(h.data(), raw[N - 1], sizeof(double2) * n, cudaMemcpyDeviceToHost));
-        double nrm = 0;
-        for (auto& v : h) nrm += v.x * v.x + v.y * v.y;
-        nrm = std::sqrt(nrm);
-        if (!(nrm > 0)) fail(TDVP_ENUMERIC, "initial state has zero norm");
-        for (auto& v : h) v = zscale(v, 1.0 / nrm);
-        CUDA_TRY(cudaMemcpy(raw[N - 1], h.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
-      }
-      // right-to-left: C = U Lambda V^dagger; Psi_j = Lambda V^dagger, V_{j-1} = 1/Lambda
-      for (int j = N - 1; j >= 1; --j) {
-        const int a = rd[j], c = rd[j + 1];
-        const int chi = device_split(S, sl, raw[j], a, d * c, chi_cap, 0.0, eps, L, S->V[j - 1], S->Psi[j],
-                                     nullptr, nullptr, s);
-        S->dims[j - 1] = chi;
-        // site j-1 <- A_{j-1} (U Lambda)
-        const int p = rd[j - 1];
-        ZGemmBatch g{};
-        g.n = 1;
-        g.d[0] = ZGemmDesc{};
-        auto& q = g.d[0];
-        q.M = p * d;
-        q.N = chi;
-        q.K = a;
-        q.A = raw[j - 1];
-        q.a_rs = a;
-        q.a_cs = 1;
-        q.B = L;
-        q.b_rs = chi;
-        q.b_cs = 1;
-        q.C = sl->theta;
-        q.c_rs = chi;
-        q.c_cs = 1;
-        launch_zgemm(g, s);
-        CUDA_TRY(cudaMemcpyAsync(raw[j - 1], sl->theta, sizeof(double2) * p * d * chi, cudaMemcpyDeviceToDevice, s));
-        rd[j] = chi;
-      }
-      CUDA_TRY(cudaMemcpyAsync(S->Psi[0], raw[0], sizeof(double2) * d * rd[1], cudaMemcpyDeviceToDevice, s));
-      CUDA_TRY(cudaStreamSynchronize(s));
+      canonicalize_device(S, raw, std::vector<int>(dims, dims + N + 1), chi_cap, eps, s);
       for (auto p : raw) dfree(p);
-      dfree(L);
-      dfree(R);
-      dfree(Vt);
     } catch (...) {
       free_mps(S);
       throw;
     }
     *out = S;
+  });
+}
+
+int tdvp_reorthonormalize(tdvp_mps mps, double eps) {
+  return ok_or_code([&] {
+    if (!mps) fail(TDVP_EINVAL, "NULL handle");
+    if (eps < 0) fail(TDVP_EINVAL, "eps < 0");
+    require_device();
+    tdvp_mps_s* S = mps;
+    cudaStream_t s = 0;
+    CUDA_TRY(cudaDeviceSynchronize());
+    const int N = S->N, d = S->d, chi_cap = S->chi_cap;
+    std::vector<int> rd(N + 1, 1);
+    for (int j = 0; j + 1 < N; ++j) rd[j + 1] = S->dims[j];
+    std::vector<double2*> raw(N);
+    for (int j = 0; j < N; ++j) {
+      raw[j] = dalloc<double2>((size_t)d * chi_cap * std::max(rd[j + 1], chi_cap) +
+                               (size_t)rd[j] * d * rd[j + 1]);
+      site_matrix(S, j, raw[j], s);  // Psi_j V_j (the last site as it is)
+    }
+    try {
+      canonicalize_device(S, raw, rd, chi_cap, eps, s);
+    } catch (...) {
+      for (auto p : raw) dfree(p);
+      throw;
+    }
+    for (auto p : raw) dfree(p);
+    S->env_id = 0;  // environments are rebuilt by the next tdvp_step / tdvp_dmrg
   });
 }
 

@@ -97,6 +97,7 @@ def lib():
         "tdvp_step": ([_P, _P, ctypes.POINTER(StepParams), ctypes.c_int, ctypes.POINTER(StepStats), _P],
                       ctypes.c_int),
         "tdvp_measure": ([_P, ctypes.c_int, _D], ctypes.c_int),
+        "tdvp_reorthonormalize": ([_P, ctypes.c_double], ctypes.c_int),
         "tdvp_dmrg": ([_P, _P, ctypes.POINTER(DmrgParams), ctypes.c_int, ctypes.POINTER(DmrgStats), _P],
                       ctypes.c_int),
         "tdvp_norm": ([_P, _D], ctypes.c_int),
@@ -297,6 +298,10 @@ def dmrg(mps: Mps, mpo: Mpo, params: DmrgParams, n_sweeps: int = 1, stream=None)
     _check(lib().tdvp_dmrg(mps.handle, mpo.handle, ctypes.byref(params), n_sweeps, ctypes.byref(st),
                            _stream(stream)))
     return st
+
+
+def reorthonormalize(mps: Mps, eps: float = 1e-14) -> None:
+    _check(lib().tdvp_reorthonormalize(mps.handle, eps))
 
 
 def measure(mps: Mps, obs: int = OBS_SZ) -> np.ndarray:

@@ -160,3 +160,75 @@ def test_step_rejects_bad_params():
     other = tdvp.build_mpo(models.ISING, N + 1, 2.0, 1.0, 1.0, 2)
     with pytest.raises(tdvp.TdvpError):
         tdvp.step(mps, other, tdvp.step_params(0.01, 8), 1)
+
+
+def test_full_size_mixed_step_matches_fp64_step():
+    """The benchmark's workload (N = 101, chi = 256, 8 segments, 8 Krylov
+    vectors, tolerance 1e-6) from its seeded random state: one mixed-precision
+    (3xTF32) step and one plain FP64 step must give <sigma^z_j> within 1e-5 (the
+    mixed path's accuracy target). The norm and the discarded weight (a sum of
+    ~1e-6 remainders over 200 splits, each carrying the contractions' ~1e-7
+    relative error of Theta') are compared loosely."""
+    torch_or_skip()
+    tdvp = lib()
+    w = I.cfg3_ising_large()
+    mdl, prm = w.model, w.params
+    mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
+    raw = I.random_mps_tensors(mdl.N, prm.chi_max, seed=0)
+    out = {}
+    for prec in (I.TF32X3, I.FP64):
+        mps = tdvp.init_mps_tensors(raw, prm.chi_max, 1e-14)
+        p = tdvp.step_params(dt=prm.dt, chi_max=prm.chi_max, w_max=prm.w_max, eps=prm.eps,
+                             krylov_max=prm.krylov_max, krylov_tol=prm.krylov_tol, precision=prec,
+                             seg_len=prm.seg_len, merge_turning=1)
+        st = tdvp.step(mps, mpo, p, 1)
+        out[prec] = (tdvp.measure(mps, tdvp.OBS_SZ), tdvp.norm(mps), st.w_total, st.chi_max_seen)
+        del mps
+    (sz_m, n_m, w_m, c_m), (sz_d, n_d, w_d, c_d) = out[I.TF32X3], out[I.FP64]
+    assert c_m == c_d == prm.chi_max
+    assert np.abs(sz_m - sz_d).max() < 1e-5
+    assert abs(n_m - n_d) < 1e-5
+    assert abs(w_m - w_d) < 0.05 * w_d
+
+
+def test_reorthonormalize_keeps_the_state():
+    """tdvp_reorthonormalize (Sec. III D) after a segmented run: the state is
+    unchanged up to its norm (observables to 1e-12), normalised (to 1e-10), and
+    back in the inverse canonical gauge (Psi_j = A_j Lambda_j = Lambda_{j-1} B_j
+    with A_j, B_j isometries); a serial run continued after it matches the
+    oracle's uninterrupted run."""
+    torch_or_skip()
+    N = 12
+    tdvp, mps, mpo, eng, W, st = run_pair(models.XY, N, 1.5, 1.0, 0.3, 4, I.basis_state("neel", N), 0.05, 6,
+                                          64, seg=[3, 3, 3, 3])
+    before = [tdvp.measure(mps, o) for o in (tdvp.OBS_SZ, tdvp.OBS_SX)]
+    tdvp.reorthonormalize(mps)
+    after = [tdvp.measure(mps, o) for o in (tdvp.OBS_SZ, tdvp.OBS_SX)]
+    for b, a in zip(before, after):
+        assert np.abs(a - b).max() < 1e-12
+    assert abs(tdvp.norm(mps) - 1.0) < 1e-10
+    # Psi_j = A_j Lambda_j = Lambda_{j-1} B_j: the Gram matrices of Psi_j over its
+    # right / left bond are Lambda^2. The check ties the SVDs of two neighbouring
+    # bonds together, and with Schmidt values down to ~1e-5 their vectors are
+    # determined to ~eps lambda_1 / lambda_i in FP64: 1e-10 of lambda_1^2
+    for j in range(N - 1):
+        psi = mps.site(j)
+        lam = 1.0 / mps.bond(j)
+        A = psi.reshape(-1, len(lam))
+        assert np.abs(A.conj().T @ A - np.diag(lam ** 2)).max() < 1e-10 * lam.max() ** 2
+    for j in range(1, N):
+        psi = mps.site(j)
+        lam = 1.0 / mps.bond(j - 1)
+        B = psi.reshape(len(lam), -1)
+        assert np.abs(B @ B.conj().T - np.diag(lam ** 2)).max() < 1e-10 * lam.max() ** 2
+    # serial: 4 steps, reorthonormalise, 4 more == 8 uninterrupted oracle steps
+    x, lam = models.fit_power_law(2.0, 4, N - 1)
+    mpo2 = tdvp.build_mpo(models.ISING, N, 2.0, 1.0, 0.8, 4, x, lam)
+    s = tdvp.init_mps(N, I.basis_state("all_up", N), 64)
+    p = tdvp.step_params(dt=0.02, chi_max=64, krylov_max=10, krylov_tol=0.0)
+    tdvp.step(s, mpo2, p, 4)
+    tdvp.reorthonormalize(s)
+    tdvp.step(s, mpo2, p, 4)
+    e = T.Engine(M.product_state(I.basis_state("all_up", N)), models.build_mpo_site(models.ISING, 1.0, 0.8, x, lam))
+    e.step(T.Params(dt=0.02, chi_max=64, krylov_max=10, krylov_tol=0.0), 8)
+    assert np.abs(tdvp.measure(s, tdvp.OBS_SZ) - M.expect_sz(e.mps)).max() < 1e-10
