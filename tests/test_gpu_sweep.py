@@ -232,3 +232,39 @@ def test_reorthonormalize_keeps_the_state():
     e = T.Engine(M.product_state(I.basis_state("all_up", N)), models.build_mpo_site(models.ISING, 1.0, 0.8, x, lam))
     e.step(T.Params(dt=0.02, chi_max=64, krylov_max=10, krylov_tol=0.0), 8)
     assert np.abs(tdvp.measure(s, tdvp.OBS_SZ) - M.expect_sz(e.mps)).max() < 1e-10
+
+
+@pytest.mark.parametrize("N,chi,seg", [(2, 4, None), (3, 4, None), (4, 1, None), (6, 8, [2, 4]), (7, 8, [3, 4])])
+def test_sweep_edge_cases(N, chi, seg):
+    """Smallest chains (a single pair; three sites), bond dimension 1 (a product
+    state kept a product state), segments of two sites and an odd chain length:
+    the same schedule and results as the oracle."""
+    tdvp, mps, mpo, eng, W, st = run_pair(models.ISING, N, 2.0, 1.0, 0.7, 2, I.basis_state("neel", N), 0.05, 3,
+                                          chi, seg=seg)
+    compare(tdvp, mps, mpo, eng, W, 1e-10)
+    assert list(mps.bond_dims()) == eng.mps.bond_dims()
+    assert st.n_fwd2 == eng.stats.n_fwd2 and st.n_back1 == eng.stats.n_back1
+
+
+def test_cfg2_full_size_properties():
+    """Config 2 at its full size (XY, N = 51, chi_max = 128, eps = 1e-10, four
+    segments 13/13/13/12, Neel start): the XY Hamiltonian conserves the total
+    S^z (+1 for the odd chain's Neel state) to rounding; the energy of the TDVP state is conserved up
+    to the truncation, and the norm drops by about the discarded weight."""
+    torch_or_skip()
+    tdvp = lib()
+    w = I.cfg2_xy_medium()
+    mdl, prm = w.model, w.params
+    mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
+    mps = tdvp.init_mps(mdl.N, I.basis_state("neel", mdl.N), prm.chi_max)
+    e0 = tdvp.energy(mps, mpo)
+    sz0 = tdvp.measure(mps, tdvp.OBS_SZ).sum()
+    p = tdvp.step_params(dt=prm.dt, chi_max=prm.chi_max, w_max=prm.w_max, eps=prm.eps, krylov_max=10,
+                         krylov_tol=0.0, seg_len=prm.seg_len)
+    st = tdvp.step(mps, mpo, p, 20)
+    sz = tdvp.measure(mps, tdvp.OBS_SZ)
+    assert abs(sz0 - 1.0) < 1e-12 and abs(sz.sum() - sz0) < 1e-9
+    assert abs(tdvp.energy(mps, mpo) - e0) < 1e-3 * max(1.0, abs(e0))
+    nrm = tdvp.norm(mps)
+    assert nrm <= 1.0 + 1e-10
+    assert st.chi_max_seen <= prm.chi_max
