@@ -16,6 +16,9 @@ Modules
              truncated split (Fig. 5, Sec. III C/D), serial and segmented sweeps
              (Sec. III A/B, App. A/B)
   ed      -- exact diagonalisation of the dense 2^N Hamiltonian
+  dmrg    -- two-site DMRG ground states with the same building blocks
+  grad    -- d<O_j(t)>/d(h, J) of the sweep: the same steps in PyTorch FP64 CPU
+             operations, differentiated by forward-mode automatic differentiation
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py
 against a closed form, a brute-force dense calculation or exact
