@@ -223,6 +223,52 @@ typedef struct {
 int tdvp_dmrg(tdvp_mps mps, tdvp_mpo mpo, const tdvp_dmrg_params* params, int n_sweeps,
               tdvp_dmrg_stats* stats, void* stream);
 
+/* ---- derivatives with respect to the model parameters ----
+ * The paper evolves in time only. These calls give d<O_j(t)>/d(h, J) of the
+ * sweep that tdvp_step runs (Sec. III A/B, Eqs. 18-20, Fig. 5) by forward-mode
+ * differentiation: every local operation of the sweep also advances a tangent
+ * (dPsi_j, dV_j, d beta_j, d gamma_j) per parameter direction, in FP64.
+ *   Theta:     dTheta = dPsi_j V Psi_{j+1} + Psi_j dV Psi_{j+1} + Psi_j V dPsi_{j+1}
+ *   exp:       d(e^{-itH} x) = e^{-itH} dx + int_0^1 e^{-istH} (-it dH) e^{-i(1-s)tH} x ds,
+ *              the integral by n_quad-point Gauss-Legendre quadrature, each exponential by
+ *              the same Lanczos settings as the primal step, dH = H_eff(d beta, W, gamma) +
+ *              H_eff(beta, dW, gamma) + H_eff(beta, W, d gamma);
+ *   split:     the derivative of the truncated SVD at fixed kept rank (all singular triplets
+ *              of Theta' enter the kept-discarded couplings);
+ *   envs:      the product rule on Eq. 19 (bra, ket and W).
+ * The derivative is that of the algorithm with exact local exponentials and a
+ * fixed truncation pattern; it agrees with finite differences of tdvp_step as long
+ * as the kept ranks do not change and the Lanczos runs are converged. */
+#define TDVP_PARAM_H 0   /* transverse field h                                     */
+#define TDVP_PARAM_J 1   /* coupling J (multiplies every exponential weight x_k)    */
+#define TDVP_MAX_DIR 4
+
+typedef struct tdvp_tangent_s* tdvp_tangent;
+
+/* dW/d(param) of `mpo` as an MPO handle (W is affine in h and J, Sec. II C), for
+ * tdvp_step_tangent. The handle may be used with tdvp_energy to get <psi|dH|psi>. */
+int tdvp_build_mpo_derivative(tdvp_mpo mpo, int param, tdvp_mpo* out);
+/* Tangent of `mps` in n_dir (<= TDVP_MAX_DIR) directions, all zero (the state
+ * does not depend on the parameters). The tangent follows the bond dimensions
+ * of `mps`; it stays valid only while `mps` is advanced by tdvp_step_tangent. */
+int tdvp_tangent_create(tdvp_mps mps, int n_dir, tdvp_tangent* out);
+void tdvp_free_tangent(tdvp_tangent tan);
+/* n_steps time steps of `mps` exactly as tdvp_step (FP64 only), advancing `tan`
+ * along dmpo[0..n_dir) (derivative MPOs of `mpo`). n_quad in [1, 8] and
+ * n_quad * n_dir <= 31. The local operations of a stage run one at a time.
+ * Errors as tdvp_step; TDVP_EINVAL for a derivative MPO of another MPO. */
+int tdvp_step_tangent(tdvp_mps mps, tdvp_mpo mpo, tdvp_tangent tan, const tdvp_mpo* dmpo,
+                      const tdvp_step_params* params, int n_quad, int n_steps, tdvp_step_stats* stats,
+                      void* stream);
+/* <O_j> (N doubles, may be NULL) and d<O_j> per direction (n_dir x N doubles,
+ * row q = direction q) for <O_j> = <psi|O_j|psi>/<psi|psi>:
+ * d<O_j> = 2 Re<psi|O_j|dpsi>/<psi|psi> - <O_j> 2 Re<psi|dpsi>/<psi|psi>.
+ * Synchronises. */
+int tdvp_measure_tangent(tdvp_mps mps, tdvp_tangent tan, int obs, double* value_out, double* d_out);
+/* Host only: n-point Gauss-Legendre nodes and weights on [0, 1] (the quadrature
+ * of tdvp_step_tangent). */
+int tdvp_gauss_legendre(int n, double* x_out, double* w_out);
+
 /* ---- measurement (Sec. IV; excluded from timing as in the paper) ---- */
 
 /* <psi|O_j|psi>/<psi|psi> for every site j (N doubles) by full transfer-matrix

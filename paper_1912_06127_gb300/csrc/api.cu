@@ -41,6 +41,8 @@ struct tdvp_mpo_s {
   std::vector<double2> W12;  // [m][m][d^2][d^2]
   DeviceWOp w1, w1t, w2;     // one-site (out right), one-site (out left), two-site
   uint64_t id = 0;
+  uint64_t base_id = 0;      // derivative MPOs: id of the MPO they differentiate
+  int param = -1;            // derivative MPOs: TDVP_PARAM_H or TDVP_PARAM_J
 };
 
 struct tdvp_mps_s {
@@ -102,14 +104,15 @@ void require_device() {
   }
 }
 
-std::vector<double2> two_site_mpo(const std::vector<double2>& W, int m, int d) {
+// W12[a][c] = sum_b W1[a][b] (x) W2[b][c] (two-site MPO tensor over pairs of sites)
+std::vector<double2> two_site_mpo(const std::vector<double2>& W1, const std::vector<double2>& W2, int m, int d) {
   const int D = d * d;
   std::vector<double2> W12((size_t)m * m * D * D, make_double2(0, 0));
   for (int a = 0; a < m; ++a)
     for (int b = 0; b < m; ++b)
       for (int c = 0; c < m; ++c) {
-        const double2* w1 = &W[((size_t)a * m + b) * d * d];
-        const double2* w2 = &W[((size_t)b * m + c) * d * d];
+        const double2* w1 = &W1[((size_t)a * m + b) * d * d];
+        const double2* w2 = &W2[((size_t)b * m + c) * d * d];
         bool nz1 = false, nz2 = false;
         for (int q = 0; q < d * d; ++q) {
           nz1 |= w1[q].x != 0 || w1[q].y != 0;
@@ -328,8 +331,11 @@ struct StageOp {
 // (Eq. 18); ground = true: Theta' = the lowest Ritz vector of H2_eff in the
 // Krylov space of Theta (two-site DMRG), its Ritz value written to *energy
 // (one problem).
+// s_full (one problem only): all singular values written there and every pair
+// of vectors converged (no tail rule), as the derivative of the split needs.
 void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, const tdvp_step_params* p,
-              tdvp_step_stats* st, cudaStream_t s, bool ground = false, double* energy = nullptr) {
+              tdvp_step_stats* st, cudaStream_t s, bool ground = false, double* energy = nullptr,
+              double* s_full = nullptr) {
   const int n = (int)ops.size();
   const int d = S->d, m = M->m, prec = p->precision;
   const double tau = 0.5 * p->dt;
@@ -420,7 +426,8 @@ void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, con
     q.PsiL = S->Psi[j];
     q.V = S->V[j];
     q.PsiR = S->Psi[j + 1];
-    q.s_sorted = nullptr;
+    q.s_sorted = n == 1 ? s_full : nullptr;
+    q.zero_rel = n == 1 && s_full ? 1e-250 : 0.0;
   }
   svd_split(sb, S->d_flag, S->h_pinned, s);
   read_stage_results(S, n, s);
@@ -804,7 +811,7 @@ int tdvp_build_mpo(const tdvp_model* model, tdvp_mpo* out) {
       host_fit_power_law(model->alpha, model->n_exp, model->N - 1, M->x, M->lam);
     }
     build_site_W(M.get());
-    M->W12 = two_site_mpo(M->W, M->m, M->d);
+    M->W12 = two_site_mpo(M->W, M->W, M->m, M->d);
     M->w1.build(M->W, M->m, M->d, false);
     M->w1t.build(M->W, M->m, M->d, true);
     M->w2.build(M->W12, M->m, M->d * M->d, false);
@@ -1163,7 +1170,7 @@ struct OpHeff {
              const double* L, const double* R, int kmax, cudaStream_t s) {
     std::vector<double2> Wd((const double2*)W, (const double2*)W + (size_t)m * m * d * d);
     const int D = nsite == 2 ? d * d : d;
-    if (nsite == 2) wop.build(two_site_mpo(Wd, m, d), m, D, false);
+    if (nsite == 2) wop.build(two_site_mpo(Wd, Wd, m, d), m, D, false);
     else wop.build(Wd, m, D, false);
     const int c = std::max(chi_l, chi_r);
     C.slot.ensure((int64_t)chi_l * D * chi_r, (int64_t)chi_l * m * D * chi_r,
@@ -1495,6 +1502,706 @@ int tdvp_op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const do
     if (!W || !L || !R || !x || !y) fail(TDVP_EINVAL, "NULL argument");
     require_device();
     op_heff_noalloc(nsite, chi_l, chi_r, m, d, W, L, R, x, y, (cudaStream_t)stream);
+  });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Forward-mode derivative of the sweep with respect to model parameters
+// ---------------------------------------------------------------------------
+constexpr int TAN_MAX_QUAD = 8;
+
+struct tdvp_tangent_s {
+  tdvp_mps_s* S = nullptr;
+  int nd = 0;
+  int N = 0, d = 2, chi_cap = 1;
+  std::vector<double2*> dPsi[TDVP_MAX_DIR];
+  std::vector<double*> dV[TDVP_MAX_DIR];
+  std::vector<double2*> dbeta[TDVP_MAX_DIR], dgamma[TDVP_MAX_DIR];
+  int env_m = 0;
+  uint64_t env_id = 0;                 // MPO whose tangent environments are held
+  std::vector<uint64_t> env_dids;      // and its derivative MPOs, per direction
+  int64_t vec = 0;                     // chi_cap^2 d^2
+  double2 *U = nullptr, *Vh = nullptr, *Am = nullptr;
+  double* s_full = nullptr;
+  double2 *dTh[TDVP_MAX_DIR] = {}, *dTh2[TDVP_MAX_DIR] = {}, *Tm[TDVP_MAX_DIR] = {}, *dP[TDVP_MAX_DIR] = {};
+  double2 *CL[TDVP_MAX_DIR] = {}, *CR[TDVP_MAX_DIR] = {}, *dAm[TDVP_MAX_DIR] = {};
+  double2* qb[TAN_MAX_QUAD] = {};
+  double2* qc[TAN_MAX_QUAD * TDVP_MAX_DIR] = {};
+
+  void free_envs() {
+    for (int q = 0; q < TDVP_MAX_DIR; ++q) {
+      for (auto p : dbeta[q]) dfree(p);
+      for (auto p : dgamma[q]) dfree(p);
+      dbeta[q].clear();
+      dgamma[q].clear();
+    }
+    env_id = 0;
+    env_m = 0;
+    env_dids.clear();
+  }
+  ~tdvp_tangent_s() {
+    cudaDeviceSynchronize();
+    for (int q = 0; q < TDVP_MAX_DIR; ++q) {
+      for (auto p : dPsi[q]) dfree(p);
+      for (auto p : dV[q]) dfree(p);
+      for (double2* p : {dTh[q], dTh2[q], Tm[q], dP[q], CL[q], CR[q], dAm[q]}) dfree(p);
+    }
+    free_envs();
+    for (auto p : qb) dfree(p);
+    for (auto p : qc) dfree(p);
+    dfree(U);
+    dfree(Vh);
+    dfree(Am);
+    dfree(s_full);
+  }
+};
+
+namespace {
+
+using Tan = tdvp_tangent_s;
+
+double2* dzeros(int64_t n) {
+  double2* p = dalloc<double2>((size_t)std::max<int64_t>(n, 1));
+  CUDA_TRY(cudaMemset(p, 0, sizeof(double2) * std::max<int64_t>(n, 1)));
+  return p;
+}
+
+// A_j = Psi_j V_j into T->Am and dA_j = dPsi_j V_j + Psi_j dV_j into T->dAm[q]
+// (side 0); B = V_j Psi_{j+1}, dB = dV_j Psi_{j+1} + V_j dPsi_{j+1} (side 1).
+void bond_mats(Tan* T, tdvp_mps_s* S, int side, int j, cudaStream_t s) {
+  const int d = S->d;
+  ScaleBatch sb{};
+  const int site = side == 0 ? j : j + 1;
+  const int A = S->chiL(site), B = S->chiR(site);
+  sb.d[sb.n++] = ScaleDesc{S->Psi[site], T->Am, S->V[j], A, d, B, side, nullptr, nullptr};
+  for (int q = 0; q < T->nd; ++q)
+    sb.d[sb.n++] = ScaleDesc{T->dPsi[q][site], T->dAm[q], S->V[j], A, d, B, side, S->Psi[site], T->dV[q][j]};
+  launch_scale_bond(sb, s);
+}
+
+// tangent of beta_{j+1} (side 0) or gamma_j (side 1) by the product rule on Eq. 19:
+// dE' = E(dE; M, M; W) + E(E; bra M, ket dM; W) + E(E; bra dM, ket M; W) + E(E; M, M; dW)
+void tangent_env(Tan* T, tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<tdvp_mpo_s*>& dM, int side, int j,
+                 cudaStream_t s) {
+  const int d = S->d, m = M->m, nd = T->nd;
+  bond_mats(T, S, side, j, s);
+  Ctx c{s, S->d_status, TDVP_FP64};
+  const int site = side == 0 ? j : j + 1;
+  const int A = S->chiL(site), B = S->chiR(site);
+  for (int term = 0; term < 4; ++term) {
+    std::vector<EnvProb> P;
+    for (int q = 0; q < nd; ++q) {
+      Slot* sl = slot_for(S, 1 + q, m, 1);
+      EnvProb e{};
+      e.A = A;
+      e.B = B;
+      e.d = d;
+      e.m = m;
+      e.slot = sl;
+      e.env = side == 0 ? (term == 0 ? T->dbeta[q][j] : S->beta[j]) : (term == 0 ? T->dgamma[q][j + 1] : S->gamma[j + 1]);
+      e.mat = term == 1 ? T->dAm[q] : T->Am;                                  // ket
+      e.bra = term == 1 ? T->Am : (term == 2 ? T->dAm[q] : nullptr);         // bra (null: = ket)
+      if (term == 3) e.W = side == 0 ? dM[q]->w1.op() : dM[q]->w1t.op();
+      else e.W = side == 0 ? M->w1.op() : M->w1t.op();
+      e.out = side == 0 ? T->dbeta[q][j + 1] : T->dgamma[q][j];
+      e.accumulate = term > 0;
+      P.push_back(e);
+    }
+    env_batch(side, P, c);
+  }
+}
+
+void tangent_alloc(Tan* T, int m) {
+  tdvp_mps_s* S = T->S;
+  if (T->env_m != m) {
+    T->free_envs();
+    for (int q = 0; q < T->nd; ++q) {
+      T->dbeta[q].resize(S->N);
+      T->dgamma[q].resize(S->N);
+      for (int j = 0; j < S->N; ++j) {
+        T->dbeta[q][j] = dzeros((int64_t)S->capL(j) * S->capL(j) * m);
+        T->dgamma[q][j] = dzeros((int64_t)S->capR(j) * S->capR(j) * m);
+      }
+    }
+    T->env_m = m;
+  }
+}
+
+// all tangent environments from scratch, with the primal ones rebuilt alongside
+void build_tangent_envs(Tan* T, tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<tdvp_mpo_s*>& dM,
+                        cudaStream_t s) {
+  build_all_envs(S, M, s);
+  tangent_alloc(T, M->m);
+  const int N = S->N, m = M->m;
+  for (int q = 0; q < T->nd; ++q) {
+    CUDA_TRY(cudaMemsetAsync(T->dbeta[q][0], 0, sizeof(double2) * m, s));
+    CUDA_TRY(cudaMemsetAsync(T->dgamma[q][N - 1], 0, sizeof(double2) * m, s));
+  }
+  for (int j = 0; j + 1 < N; ++j) tangent_env(T, S, M, dM, 0, j, s);
+  for (int j = N - 2; j >= 0; --j) tangent_env(T, S, M, dM, 1, j, s);
+  T->env_id = M->id;
+  T->env_dids.clear();
+  for (auto* p : dM) T->env_dids.push_back(p->id);
+}
+
+// d(exp(-i t H) x) for H = H_eff(L, W, R) of one local problem and every
+// direction q: dy_q = exp(-i t H) dx_q + sum_n w_n (-i t) exp(-i s_n t H) dH_q exp(-i (1 - s_n) t H) x.
+// x: primal input (unchanged); dx[q] -> dy[q] (may alias). base: the primal
+// MvProb; dL/dR/dWop: tangent environments and derivative MPO operators.
+void tangent_expm(Tan* T, tdvp_mps_s* S, const MvProb& base, const double2* x, const std::vector<double2*>& dx,
+                  const std::vector<double2*>& dy, const std::vector<const double2*>& dL,
+                  const std::vector<const double2*>& dR, const std::vector<WOp>& dWop, double t,
+                  const std::vector<double>& xq, const std::vector<double>& wq, const tdvp_step_params* p,
+                  int m, cudaStream_t s) {
+  const int nd = T->nd, nq = (int)xq.size();
+  Ctx c{s, S->d_status, TDVP_FP64};
+  // exp(-i (1 - s_n) t H) x and exp(-i t H) dx_q
+  {
+    std::vector<MvProb> P;
+    std::vector<const double2*> xi;
+    std::vector<double2*> yo;
+    std::vector<double> tt;
+    for (int n = 0; n < nq; ++n) {
+      MvProb q = base;
+      q.slot = slot_for(S, 1 + P.size(), m, p->krylov_max);
+      P.push_back(q);
+      xi.push_back(x);
+      yo.push_back(T->qb[n]);
+      tt.push_back((1.0 - xq[n]) * t);
+    }
+    for (int k = 0; k < nd; ++k) {
+      MvProb q = base;
+      q.slot = slot_for(S, 1 + P.size(), m, p->krylov_max);
+      P.push_back(q);
+      xi.push_back(dx[k]);
+      yo.push_back(dy[k]);
+      tt.push_back(t);
+    }
+    expm_batch(P, xi, yo, tt, p->krylov_max, p->krylov_tol, c);
+  }
+  // c_{n,q} = dH_q b_n (three H_eff products, summed)
+  for (int term = 0; term < 3; ++term) {
+    std::vector<MvProb> P;
+    std::vector<const double2*> xi;
+    std::vector<double2*> yo;
+    for (int n = 0; n < nq; ++n)
+      for (int k = 0; k < nd; ++k) {
+        MvProb q = base;
+        q.slot = slot_for(S, 1 + P.size(), m, p->krylov_max);
+        if (term == 0) q.L = dL[k];
+        if (term == 1) q.W = dWop[k];
+        if (term == 2) q.R = dR[k];
+        P.push_back(q);
+        xi.push_back(T->qb[n]);
+        yo.push_back(T->qc[n * nd + k]);
+      }
+    matvec_batch(P, xi, yo, c, term > 0);
+  }
+  // exp(-i s_n t H) c_{n,q}, in place
+  {
+    std::vector<MvProb> P;
+    std::vector<const double2*> xi;
+    std::vector<double2*> yo;
+    std::vector<double> tt;
+    for (int n = 0; n < nq; ++n)
+      for (int k = 0; k < nd; ++k) {
+        MvProb q = base;
+        q.slot = slot_for(S, 1 + P.size(), m, p->krylov_max);
+        P.push_back(q);
+        xi.push_back(T->qc[n * nd + k]);
+        yo.push_back(T->qc[n * nd + k]);
+        tt.push_back(xq[n] * t);
+      }
+    expm_batch(P, xi, yo, tt, p->krylov_max, p->krylov_tol, c);
+  }
+  ZCombBatch zb{};
+  const int64_t len = (int64_t)base.A * base.D * base.B;
+  for (int k = 0; k < nd; ++k) {
+    ZCombDesc& z = zb.d[zb.n++];
+    z = ZCombDesc{};
+    z.y = dy[k];
+    z.n = len;
+    z.accumulate = 1;
+    z.n_terms = nq;
+    for (int n = 0; n < nq; ++n) {
+      z.x[n] = T->qc[n * nd + k];
+      z.c[n] = make_double2(0.0, -t * wq[n]);
+    }
+  }
+  launch_zcombine(zb, s);
+}
+
+void tangent_fwd2(Tan* T, tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<tdvp_mpo_s*>& dM, const StageOp& op,
+                  const tdvp_step_params* p, const std::vector<double>& xq, const std::vector<double>& wq,
+                  tdvp_step_stats* st, cudaStream_t s) {
+  const int j = op.j, d = S->d, m = M->m, nd = T->nd;
+  const double t = op.tfac * 0.5 * p->dt;
+  {
+    // dTheta = dPsi_j V_j Psi_{j+1} + Psi_j dV_j Psi_{j+1} + Psi_j V_j dPsi_{j+1}
+    const int A = S->chiL(j), cb = S->dims[j], B = S->chiR(j + 1);
+    for (int term = 0; term < 3; ++term) {
+      ZGemmBatch g{};
+      g.n = nd;
+      for (int q = 0; q < nd; ++q) {
+        ZGemmDesc& z = g.d[q];
+        z = ZGemmDesc{};
+        z.M = A * d;
+        z.N = d * B;
+        z.K = cb;
+        z.A = term == 0 ? T->dPsi[q][j] : S->Psi[j];
+        z.a_rs = cb;
+        z.a_cs = 1;
+        z.kscale = term == 1 ? T->dV[q][j] : S->V[j];
+        z.B = term == 2 ? T->dPsi[q][j + 1] : S->Psi[j + 1];
+        z.b_rs = (int64_t)d * B;
+        z.b_cs = 1;
+        z.C = T->dTh[q];
+        z.c_rs = (int64_t)d * B;
+        z.c_cs = 1;
+        z.accumulate = term > 0;
+      }
+      launch_zgemm(g, s, "tangent_zgemm");
+    }
+  }
+  // the primal update, with the full SVD kept converged
+  run_fwd2(S, M, {op}, p, st, s, false, nullptr, T->s_full);
+  Slot* s0 = S->slots[0].get();
+  const int A = S->chiL(j), B = S->chiR(j + 1), k = S->dims[j];
+  // d(exp(-i t H2_eff) Theta)
+  {
+    MvProb base = make_mv(S, M, A, B, d * d, j, j + 1, true, s0, TDVP_FP64);
+    std::vector<double2*> dx, dy;
+    std::vector<const double2*> dL, dR;
+    std::vector<WOp> dW;
+    for (int q = 0; q < nd; ++q) {
+      dx.push_back(T->dTh[q]);
+      dy.push_back(T->dTh2[q]);
+      dL.push_back(T->dbeta[q][j]);
+      dR.push_back(T->dgamma[q][j + 1]);
+      dW.push_back(dM[q]->w2.op());
+    }
+    tangent_expm(T, S, base, s0->theta, dx, dy, dL, dR, dW, t, xq, wq, p, m, s);
+  }
+  // derivative of the truncated split
+  const int rows = A * d, cols = d * B;
+  const int trans = rows > cols ? 1 : 0;
+  const int r = trans ? cols : rows, len = trans ? rows : cols;
+  launch_svd_export_full(SvdFullDesc{s0->svdX, s0->svdAcc, s0->sig, s0->perm, rows, cols, r, len, trans, T->U, T->Vh,
+                                     T->s_full},
+                         s);
+  auto gemm_batch = [&](auto fill, const char* name) {
+    ZGemmBatch g{};
+    g.n = nd;
+    for (int q = 0; q < nd; ++q) {
+      g.d[q] = ZGemmDesc{};
+      fill(g.d[q], q);
+      g.d[q].c_cs = 1;
+    }
+    launch_zgemm(g, s, name);
+  };
+  // Tm = dTheta' V (rows x r), dP = U^H Tm (r x r)
+  gemm_batch([&](ZGemmDesc& z, int q) {
+    z.M = rows; z.N = r; z.K = cols;
+    z.A = T->dTh2[q]; z.a_rs = cols; z.a_cs = 1;
+    z.B = T->Vh; z.b_rs = 1; z.b_cs = cols; z.conj_b = 1;
+    z.C = T->Tm[q]; z.c_rs = r;
+  }, "tangent_zgemm");
+  gemm_batch([&](ZGemmDesc& z, int q) {
+    z.M = r; z.N = r; z.K = rows;
+    z.A = T->U; z.a_rs = 1; z.a_cs = r; z.conj_a = 1;
+    z.B = T->Tm[q]; z.b_rs = r; z.b_cs = 1;
+    z.C = T->dP[q]; z.c_rs = r;
+  }, "tangent_zgemm");
+  {
+    SvdTanBatch tb{};
+    tb.n = nd;
+    for (int q = 0; q < nd; ++q) tb.d[q] = SvdTanDesc{T->dP[q], T->s_full, r, k, T->CL[q], T->CR[q], T->dV[q][j]};
+    launch_svd_tangent_coef(tb, s);
+  }
+  // dPsi_L = dTheta' V_k + U CL   (rows x k)
+  gemm_batch([&](ZGemmDesc& z, int q) {
+    z.M = rows; z.N = k; z.K = cols;
+    z.A = T->dTh2[q]; z.a_rs = cols; z.a_cs = 1;
+    z.B = T->Vh; z.b_rs = 1; z.b_cs = cols; z.conj_b = 1;
+    z.C = T->dPsi[q][j]; z.c_rs = k;
+  }, "tangent_zgemm");
+  gemm_batch([&](ZGemmDesc& z, int q) {
+    z.M = rows; z.N = k; z.K = r;
+    z.A = T->U; z.a_rs = r; z.a_cs = 1;
+    z.B = T->CL[q]; z.b_rs = k; z.b_cs = 1;
+    z.C = T->dPsi[q][j]; z.c_rs = k; z.accumulate = 1;
+  }, "tangent_zgemm");
+  // dPsi_R = CR^H V^H + U_k^H dTheta'   (k x cols)
+  gemm_batch([&](ZGemmDesc& z, int q) {
+    z.M = k; z.N = cols; z.K = r;
+    z.A = T->CR[q]; z.a_rs = 1; z.a_cs = k; z.conj_a = 1;
+    z.B = T->Vh; z.b_rs = cols; z.b_cs = 1;
+    z.C = T->dPsi[q][j + 1]; z.c_rs = cols;
+  }, "tangent_zgemm");
+  gemm_batch([&](ZGemmDesc& z, int q) {
+    z.M = k; z.N = cols; z.K = rows;
+    z.A = T->U; z.a_rs = 1; z.a_cs = r; z.conj_a = 1;
+    z.B = T->dTh2[q]; z.b_rs = cols; z.b_cs = 1;
+    z.C = T->dPsi[q][j + 1]; z.c_rs = cols; z.accumulate = 1;
+  }, "tangent_zgemm");
+  if (op.env & 1) tangent_env(T, S, M, dM, 0, j, s);
+  if (op.env & 2) tangent_env(T, S, M, dM, 1, j, s);
+}
+
+void tangent_back1(Tan* T, tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<tdvp_mpo_s*>& dM, const StageOp& op,
+                   const tdvp_step_params* p, const std::vector<double>& xq, const std::vector<double>& wq,
+                   tdvp_step_stats* st, cudaStream_t s) {
+  const int j = op.j, d = S->d, m = M->m, nd = T->nd;
+  const double t = -op.tfac * 0.5 * p->dt;
+  const int A = S->chiL(j), B = S->chiR(j);
+  Slot* s0 = slot_for(S, 0, m, p->krylov_max);
+  MvProb base = make_mv(S, M, A, B, d, j, j, false, s0, TDVP_FP64);
+  std::vector<double2*> dx;
+  std::vector<const double2*> dL, dR;
+  std::vector<WOp> dW;
+  for (int q = 0; q < nd; ++q) {
+    dx.push_back(T->dPsi[q][j]);
+    dL.push_back(T->dbeta[q][j]);
+    dR.push_back(T->dgamma[q][j]);
+    dW.push_back(dM[q]->w1.op());
+  }
+  tangent_expm(T, S, base, S->Psi[j], dx, dx, dL, dR, dW, t, xq, wq, p, m, s);
+  run_back1(S, M, {op}, p, st, s);
+}
+
+void tangent_workspace(Tan* T) {
+  if (T->U) return;
+  const int64_t v = T->vec;
+  T->U = dzeros(v);
+  T->Vh = dzeros(v);
+  T->Am = dzeros(v);
+  T->s_full = dalloc<double>((size_t)T->chi_cap * T->d);
+  for (int q = 0; q < T->nd; ++q) {
+    T->dTh[q] = dzeros(v);
+    T->dTh2[q] = dzeros(v);
+    T->Tm[q] = dzeros(v);
+    T->dP[q] = dzeros(v);
+    T->CL[q] = dzeros(v);
+    T->CR[q] = dzeros(v);
+    T->dAm[q] = dzeros(v);
+  }
+  for (int n = 0; n < TAN_MAX_QUAD; ++n) T->qb[n] = dzeros(v);
+  for (int n = 0; n < TAN_MAX_QUAD * T->nd; ++n) T->qc[n] = dzeros(v);
+}
+
+void step_tangent_impl(tdvp_mps_s* S, tdvp_mpo_s* M, Tan* T, const tdvp_mpo* dmpo, const tdvp_step_params* p,
+                       int nq, int n_steps, tdvp_step_stats* st, cudaStream_t s) {
+  check_params(S, M, p);
+  if (T->S != S) fail(TDVP_EINVAL, "tangent belongs to another MPS");
+  if (p->precision != TDVP_FP64) fail(TDVP_EINVAL, "derivatives are computed in FP64 only");
+  if (nq < 1 || nq > TAN_MAX_QUAD || nq * T->nd > MAXB - 1 || nq + T->nd > MAXB - 1)
+    fail(TDVP_EINVAL, "n_quad must be in [1, 8] with n_quad * n_dir <= 31");
+  if (!dmpo) fail(TDVP_EINVAL, "NULL derivative MPO list");
+  std::vector<tdvp_mpo_s*> dM(T->nd);
+  for (int q = 0; q < T->nd; ++q) {
+    dM[q] = dmpo[q];
+    if (!dM[q] || dM[q]->base_id != M->id || dM[q]->m != M->m)
+      fail(TDVP_EINVAL, "derivative MPO does not belong to this MPO");
+  }
+  ensure_small_buffers(S);
+  tangent_workspace(T);
+  std::vector<double> xq, wq;
+  gauss_legendre01(nq, xq, wq);
+  std::vector<int> seg;
+  if (p->n_seg <= 1 || !p->seg_len) seg = {S->N};
+  else seg.assign(p->seg_len, p->seg_len + p->n_seg);
+  if ((int)seg.size() > MAXB) fail(TDVP_EINVAL, "too many segments");
+  std::vector<SchedOp> halves[2];
+  build_half(S->N, seg, 1, p->merge_turning, halves[0]);
+  build_half(S->N, seg, 2, p->merge_turning, halves[1]);
+  const int64_t l0 = g_launches;
+  bool fresh = T->env_id != M->id || S->env_id != M->id || (int)T->env_dids.size() != T->nd;
+  for (int q = 0; q < T->nd && !fresh; ++q) fresh = T->env_dids[q] != dM[q]->id;
+  if (fresh) build_tangent_envs(T, S, M, dM, s);
+  for (int step = 0; step < n_steps; ++step) {
+    for (int h = 0; h < 2; ++h) {
+      const auto& ops = halves[h];
+      size_t i = 0;
+      while (i < ops.size()) {
+        const int stage = ops[i].stage;
+        std::vector<StageOp> f, b;
+        while (i < ops.size() && ops[i].stage == stage) {
+          if (ops[i].kind == 0) f.push_back(StageOp{ops[i].j, ops[i].tfac, ops[i].env});
+          else b.push_back(StageOp{ops[i].j, ops[i].tfac, 0});
+          ++i;
+        }
+        for (auto& o : f) tangent_fwd2(T, S, M, dM, o, p, xq, wq, st, s);
+        for (auto& o : b) tangent_back1(T, S, M, dM, o, p, xq, wq, st, s);
+        if (st) st->n_stages += 1;
+      }
+    }
+    read_stage_results(S, 0, s);
+  }
+  if (st) st->kernel_launches += g_launches - l0;
+}
+
+// left transfer with accumulation: out (+)= sum conj(Ma[a,s,b]) E[a,a'] Mb[a',s,b']
+void transfer_left_acc(const double2* E, const double2* Ma, const double2* Mb, int Aa, int Ab, int d, int Ba, int Bb,
+                       double2* X, double2* out, bool acc, cudaStream_t s) {
+  run1(gemm(Aa, d * Bb, Ab, E, Ab, 1, 0, Mb, (int64_t)d * Bb, 1, X, (int64_t)d * Bb), s);
+  ZGemmDesc g = gemm(Ba, Bb, Aa * d, Ma, 1, Ba, 1, X, Bb, 1, out, Bb);
+  g.accumulate = acc;
+  run1(g, s);
+}
+
+// right transfer with accumulation: out[a][a'] (+)= sum conj(Ma[a,s,b]) Mb[a',s,b'] E[b][b']
+void transfer_right_acc(const double2* E, const double2* Ma, const double2* Mb, int A, int d, int B, double2* Y,
+                        double2* out, bool acc, cudaStream_t s) {
+  run1(gemm(A * d, B, B, Mb, B, 1, 0, E, 1, B, Y, B), s);
+  ZGemmDesc g = gemm(A, A, d * B, Ma, (int64_t)d * B, 1, 1, Y, 1, (int64_t)d * B, out, A);
+  g.accumulate = acc;
+  run1(g, s);
+}
+
+void measure_tangent_impl(tdvp_mps_s* S, Tan* T, const double2 op[4], double* val_out, double* d_out) {
+  cudaStream_t s = 0;
+  const int N = S->N, d = S->d, nd = T->nd;
+  const int64_t big = (int64_t)S->chi_cap * d * S->chi_cap;
+  MeasureBufs mb;
+  mb.Mj = dalloc<double2>(big);
+  mb.X = dalloc<double2>(big);
+  mb.Y = dalloc<double2>(big);
+  mb.rho = dalloc<double2>((size_t)16 * N * (1 + nd));
+  std::vector<double2*> own;
+  auto take = [&](int64_t n) {
+    own.push_back(dalloc<double2>((size_t)std::max<int64_t>(n, 1)));
+    return own.back();
+  };
+  struct Guard {
+    std::vector<double2*>& v;
+    ~Guard() {
+      for (auto p : v) dfree(p);
+    }
+  } guard{own};
+  std::vector<double2*> dMj(nd), dEL[TDVP_MAX_DIR], dER[TDVP_MAX_DIR];
+  for (int q = 0; q < nd; ++q) dMj[q] = take(big);
+  double2* X2 = take(big);
+  mb.EL.resize(N + 1);
+  mb.ER.resize(N);
+  for (int j = 0; j <= N; ++j) {
+    const int c = j == 0 ? 1 : S->chiR(j - 1);
+    mb.EL[j] = dalloc<double2>((size_t)c * c);
+    for (int q = 0; q < nd; ++q) dEL[q].push_back(take((int64_t)c * c));
+  }
+  for (int j = 0; j < N; ++j) {
+    const int c = S->chiR(j);
+    mb.ER[j] = dalloc<double2>((size_t)c * c);
+    for (int q = 0; q < nd; ++q) dER[q].push_back(take((int64_t)c * c));
+  }
+  const double2 one = make_double2(1, 0);
+  CUDA_TRY(cudaMemcpy(mb.EL[0], &one, sizeof(double2), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(mb.ER[N - 1], &one, sizeof(double2), cudaMemcpyHostToDevice));
+  for (int q = 0; q < nd; ++q) {
+    CUDA_TRY(cudaMemset(dEL[q][0], 0, sizeof(double2)));
+    CUDA_TRY(cudaMemset(dER[q][N - 1], 0, sizeof(double2)));
+  }
+  // M_j = Psi_j V_j and dM_j = dPsi_j V_j + Psi_j dV_j (the last site: Psi_N, dPsi_N)
+  auto site_mats = [&](int j) {
+    site_matrix(S, j, mb.Mj, s);
+    const int A = S->chiL(j), B = S->chiR(j);
+    for (int q = 0; q < nd; ++q) {
+      if (j == N - 1) {
+        CUDA_TRY(cudaMemcpyAsync(dMj[q], T->dPsi[q][j], sizeof(double2) * A * d * B, cudaMemcpyDeviceToDevice, s));
+      } else {
+        ScaleBatch sb{};
+        sb.n = 1;
+        sb.d[0] = ScaleDesc{T->dPsi[q][j], dMj[q], S->V[j], A, d, B, 0, S->Psi[j], T->dV[q][j]};
+        launch_scale_bond(sb, s);
+      }
+    }
+  };
+  for (int j = 0; j < N; ++j) {
+    site_mats(j);
+    const int A = S->chiL(j), B = S->chiR(j);
+    transfer_left_acc(mb.EL[j], mb.Mj, mb.Mj, A, A, d, B, B, mb.X, mb.EL[j + 1], false, s);
+    for (int q = 0; q < nd; ++q) {
+      transfer_left_acc(dEL[q][j], mb.Mj, mb.Mj, A, A, d, B, B, mb.X, dEL[q][j + 1], false, s);
+      transfer_left_acc(mb.EL[j], mb.Mj, dMj[q], A, A, d, B, B, mb.X, dEL[q][j + 1], true, s);
+    }
+  }
+  for (int j = N - 1; j >= 1; --j) {
+    site_mats(j);
+    const int A = S->chiL(j), B = S->chiR(j);
+    transfer_right_acc(mb.ER[j], mb.Mj, mb.Mj, A, d, B, mb.Y, mb.ER[j - 1], false, s);
+    for (int q = 0; q < nd; ++q) {
+      transfer_right_acc(dER[q][j], mb.Mj, mb.Mj, A, d, B, mb.Y, dER[q][j - 1], false, s);
+      transfer_right_acc(mb.ER[j], mb.Mj, dMj[q], A, d, B, mb.Y, dER[q][j - 1], true, s);
+    }
+  }
+  for (int j = 0; j < N; ++j) {
+    site_mats(j);
+    const int A = S->chiL(j), B = S->chiR(j);
+    // X2 = EL M, Y = X2 ER: <psi| (|s><s'| at j) |psi>
+    run1(gemm(A, d * B, A, mb.EL[j], A, 1, 0, mb.Mj, (int64_t)d * B, 1, X2, (int64_t)d * B), s);
+    run1(gemm(A * d, B, B, X2, B, 1, 0, mb.ER[j], 1, B, mb.Y, B), s);
+    rho_kernel<<<d * d, 256, 0, s>>>(mb.Mj, mb.Y, A, d, B, mb.rho + (size_t)16 * j);
+    LAUNCH_CHECK();
+    for (int q = 0; q < nd; ++q) {
+      // X = dEL M + EL dM; Y = X ER + X2 dER: <psi| (|s><s'| at j) |dpsi>
+      run1(gemm(A, d * B, A, dEL[q][j], A, 1, 0, mb.Mj, (int64_t)d * B, 1, mb.X, (int64_t)d * B), s);
+      ZGemmDesc g = gemm(A, d * B, A, mb.EL[j], A, 1, 0, dMj[q], (int64_t)d * B, 1, mb.X, (int64_t)d * B);
+      g.accumulate = 1;
+      run1(g, s);
+      run1(gemm(A * d, B, B, mb.X, B, 1, 0, mb.ER[j], 1, B, mb.Y, B), s);
+      g = gemm(A * d, B, B, X2, B, 1, 0, dER[q][j], 1, B, mb.Y, B);
+      g.accumulate = 1;
+      run1(g, s);
+      rho_kernel<<<d * d, 256, 0, s>>>(mb.Mj, mb.Y, A, d, B, mb.rho + (size_t)16 * (N * (1 + q) + j));
+      LAUNCH_CHECK();
+    }
+  }
+  std::vector<double2> rho((size_t)16 * N * (1 + nd));
+  CUDA_TRY(cudaMemcpy(rho.data(), mb.rho, sizeof(double2) * rho.size(), cudaMemcpyDeviceToHost));
+  double2 nrm;
+  CUDA_TRY(cudaMemcpy(&nrm, mb.EL[N], sizeof(double2), cudaMemcpyDeviceToHost));
+  if (!(nrm.x > 0)) fail(TDVP_ENUMERIC, "state has zero norm");
+  std::vector<double2> dn(nd);
+  for (int q = 0; q < nd; ++q) CUDA_TRY(cudaMemcpy(&dn[q], dEL[q][N], sizeof(double2), cudaMemcpyDeviceToHost));
+  auto contract = [&](size_t base) {
+    double2 v = make_double2(0, 0);
+    for (int k = 0; k < d * d; ++k) v = zadd(v, zmul(rho[base + k], op[k]));
+    return v;
+  };
+  for (int j = 0; j < N; ++j) {
+    const double val = contract((size_t)16 * j).x / nrm.x;
+    if (val_out) val_out[j] = val;
+    for (int q = 0; q < nd; ++q) {
+      const double2 od = contract((size_t)16 * (N * (1 + q) + j));
+      d_out[(size_t)q * N + j] = 2.0 * od.x / nrm.x - val * 2.0 * dn[q].x / nrm.x;
+    }
+  }
+}
+
+void pauli(int obs, double2 op[4]) {
+  const double2 Z = make_double2(0, 0), One = make_double2(1, 0);
+  if (obs == TDVP_OBS_SZ) {
+    op[0] = One; op[1] = Z; op[2] = Z; op[3] = make_double2(-1, 0);
+  } else if (obs == TDVP_OBS_SX) {
+    op[0] = Z; op[1] = One; op[2] = One; op[3] = Z;
+  } else if (obs == TDVP_OBS_SY) {
+    op[0] = Z; op[1] = make_double2(0, -1); op[2] = make_double2(0, 1); op[3] = Z;
+  } else {
+    fail(TDVP_EINVAL, "unknown observable");
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdvp_build_mpo_derivative(tdvp_mpo mpo, int param, tdvp_mpo* out) {
+  return ok_or_code([&] {
+    if (!mpo || !out) fail(TDVP_EINVAL, "NULL argument");
+    if (mpo->base_id) fail(TDVP_EINVAL, "already a derivative MPO");
+    if (param != TDVP_PARAM_H && param != TDVP_PARAM_J) fail(TDVP_EINVAL, "unknown parameter");
+    require_device();
+    auto D = std::make_unique<tdvp_mpo_s>();
+    D->kind = mpo->kind;
+    D->N = mpo->N;
+    D->m = mpo->m;
+    D->d = mpo->d;
+    D->n_exp = mpo->n_exp;
+    D->alpha = mpo->alpha;
+    D->x = mpo->x;
+    D->lam = mpo->lam;
+    // W is affine in (J, h): its derivative is W at (J, h) = (1, 0) or (0, 1)
+    // minus W at (0, 0) -- the coupling blocks W[c][0] or the field block W[m-1][0]
+    tdvp_mpo_s a, b;
+    a.kind = b.kind = mpo->kind;
+    a.m = b.m = mpo->m;
+    a.d = b.d = mpo->d;
+    a.n_exp = b.n_exp = mpo->n_exp;
+    a.x = b.x = mpo->x;
+    a.lam = b.lam = mpo->lam;
+    a.J = param == TDVP_PARAM_J ? 1.0 : 0.0;
+    a.h = param == TDVP_PARAM_H ? 1.0 : 0.0;
+    b.J = b.h = 0.0;
+    build_site_W(&a);
+    build_site_W(&b);
+    D->W.resize(a.W.size());
+    for (size_t i = 0; i < a.W.size(); ++i) D->W[i] = make_double2(a.W[i].x - b.W[i].x, a.W[i].y - b.W[i].y);
+    D->J = a.J;
+    D->h = a.h;
+    // d(W W) = dW W + W dW
+    auto t1 = two_site_mpo(D->W, mpo->W, D->m, D->d);
+    auto t2 = two_site_mpo(mpo->W, D->W, D->m, D->d);
+    D->W12.resize(t1.size());
+    for (size_t i = 0; i < t1.size(); ++i) D->W12[i] = zadd(t1[i], t2[i]);
+    D->w1.build(D->W, D->m, D->d, false);
+    D->w1t.build(D->W, D->m, D->d, true);
+    D->w2.build(D->W12, D->m, D->d * D->d, false);
+    D->base_id = mpo->id;
+    D->param = param;
+    {
+      std::lock_guard<std::mutex> g(g_id_mutex);
+      D->id = g_next_id++;
+    }
+    *out = D.release();
+  });
+}
+
+int tdvp_tangent_create(tdvp_mps mps, int n_dir, tdvp_tangent* out) {
+  return ok_or_code([&] {
+    if (!mps || !out) fail(TDVP_EINVAL, "NULL argument");
+    if (n_dir < 1 || n_dir > TDVP_MAX_DIR) fail(TDVP_EINVAL, "n_dir must be in [1, TDVP_MAX_DIR]");
+    require_device();
+    auto T = std::make_unique<tdvp_tangent_s>();
+    T->S = mps;
+    T->nd = n_dir;
+    T->N = mps->N;
+    T->d = mps->d;
+    T->chi_cap = mps->chi_cap;
+    T->vec = (int64_t)mps->chi_cap * mps->chi_cap * mps->d * mps->d;
+    for (int q = 0; q < n_dir; ++q) {
+      for (int j = 0; j < mps->N; ++j) T->dPsi[q].push_back(dzeros((int64_t)mps->capL(j) * mps->d * mps->capR(j)));
+      for (int j = 0; j + 1 < mps->N; ++j) {
+        double* v = dalloc<double>((size_t)mps->cap[j]);
+        CUDA_TRY(cudaMemset(v, 0, sizeof(double) * mps->cap[j]));
+        T->dV[q].push_back(v);
+      }
+    }
+    *out = T.release();
+  });
+}
+
+void tdvp_free_tangent(tdvp_tangent tan) { delete tan; }
+
+int tdvp_step_tangent(tdvp_mps mps, tdvp_mpo mpo, tdvp_tangent tan, const tdvp_mpo* dmpo,
+                      const tdvp_step_params* params, int n_quad, int n_steps, tdvp_step_stats* stats,
+                      void* stream) {
+  return ok_or_code([&] {
+    if (!mps || !mpo || !tan) fail(TDVP_EINVAL, "NULL handle");
+    if (n_steps < 0) fail(TDVP_EINVAL, "n_steps < 0");
+    step_tangent_impl(mps, mpo, tan, dmpo, params, n_quad, n_steps, stats, (cudaStream_t)stream);
+  });
+}
+
+int tdvp_measure_tangent(tdvp_mps mps, tdvp_tangent tan, int obs, double* value_out, double* d_out) {
+  return ok_or_code([&] {
+    if (!mps || !tan || !d_out) fail(TDVP_EINVAL, "NULL argument");
+    if (tan->S != mps) fail(TDVP_EINVAL, "tangent belongs to another MPS");
+    if (mps->d != 2) fail(TDVP_EINVAL, "Pauli observables need d = 2");
+    double2 op[4];
+    pauli(obs, op);
+    CUDA_TRY(cudaDeviceSynchronize());
+    measure_tangent_impl(mps, tan, op, value_out, d_out);
+  });
+}
+
+int tdvp_gauss_legendre(int n, double* x_out, double* w_out) {
+  return ok_or_code([&] {
+    if (n < 1 || n > 64 || !x_out || !w_out) fail(TDVP_EINVAL, "need 1 <= n <= 64 and outputs");
+    std::vector<double> x, w;
+    gauss_legendre01(n, x, w);
+    std::copy(x.begin(), x.end(), x_out);
+    std::copy(w.begin(), w.end(), w_out);
   });
 }
 

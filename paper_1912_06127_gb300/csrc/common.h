@@ -179,6 +179,8 @@ struct ScaleDesc {
   double2* dst;
   const double* v;
   int rows, d, cols, left;
+  const double2* src2;  // optional: dst = src v + src2 v2 (tangent of a bond scaling)
+  const double* v2;
 };
 struct ScaleBatch {
   int n;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <memory>
+#include <vector>
 
 #include "common.h"
 #include "lanczos.h"
@@ -80,8 +81,9 @@ struct Ctx {
   int prec;
 };
 
+// y = H_eff x; accumulate (FP64 only): y += H_eff x
 void matvec_batch(const std::vector<MvProb>& P, const std::vector<const double2*>& x,
-                  const std::vector<double2*>& y, const Ctx& c);
+                  const std::vector<double2*>& y, const Ctx& c, bool accumulate = false);
 void expm_batch(const std::vector<MvProb>& P, const std::vector<const double2*>& x,
                 const std::vector<double2*>& y, const std::vector<double>& t, int kmax, double tol,
                 const Ctx& c, bool ground = false);
@@ -94,6 +96,8 @@ struct EnvProb {
   double2* out;
   WOp W;      // left: out index w_right; right: out index w_left
   Slot* slot;
+  const double2* bra = nullptr;  // conjugated tensor when it differs from mat (FP64 only)
+  int accumulate = 0;            // out += ... (FP64 only)
 };
 void env_batch(int side, const std::vector<EnvProb>& P, const Ctx& c);
 // Mixed operand forms of environments: L as A operand [(a w)][pad4(2a)],
@@ -108,5 +112,45 @@ struct EnvFormJob {
 };
 void prep_L_forms(const std::vector<EnvFormJob>& jobs, cudaStream_t s);
 void prep_R_forms(const std::vector<EnvFormJob>& jobs, cudaStream_t s);
+
+// ---- forward-mode derivative of the sweep (tangent.cu) ----
+struct SvdFullDesc {
+  const double2* X;
+  const double2* Acc;
+  const double* sig;
+  const int* perm;
+  int rows, cols, n_vec, len, trans;
+  double2* U;   // [rows][n_vec]
+  double2* Vh;  // [n_vec][cols]
+  double* s;    // [n_vec], descending
+};
+void launch_svd_export_full(const SvdFullDesc& d, cudaStream_t s);
+struct SvdTanDesc {
+  const double2* dP;  // [r][r] = U^H dTheta V
+  const double* s;    // [r] descending
+  int r, k;
+  double2* CL;        // [r][k]
+  double2* CR;        // [r][k]
+  double* dV;         // [k]
+};
+struct SvdTanBatch {
+  int n;
+  SvdTanDesc d[MAXB];
+};
+void launch_svd_tangent_coef(const SvdTanBatch& b, cudaStream_t s);
+constexpr int ZCOMB_MAX = 17;
+struct ZCombDesc {
+  double2* y;
+  int64_t n;
+  int n_terms, accumulate;
+  const double2* x[ZCOMB_MAX];
+  double2 c[ZCOMB_MAX];
+};
+struct ZCombBatch {
+  int n;
+  ZCombDesc d[8];
+};
+void launch_zcombine(const ZCombBatch& b, cudaStream_t s);
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
 
 }  // namespace tdvp

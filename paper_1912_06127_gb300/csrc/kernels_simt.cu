@@ -378,7 +378,14 @@ __global__ void scale_bond_kernel(const __grid_constant__ ScaleBatch batch) {
     int r = (int)(i / ((int64_t)P.d * P.cols));
     double sc = P.left ? P.v[r] : P.v[c];
     double2 x = P.src[i];
-    P.dst[i] = make_double2(x.x * sc, x.y * sc);
+    double2 o = make_double2(x.x * sc, x.y * sc);
+    if (P.src2) {
+      const double s2 = P.left ? P.v2[r] : P.v2[c];
+      const double2 x2 = P.src2[i];
+      o.x = fma(x2.x, s2, o.x);
+      o.y = fma(x2.y, s2, o.y);
+    }
+    P.dst[i] = o;
   }
 }
 

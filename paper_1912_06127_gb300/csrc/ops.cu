@@ -211,10 +211,11 @@ void prep_R_forms(const std::vector<EnvFormJob>& jobs, cudaStream_t s) {
 // H_eff . x for a batch
 // ---------------------------------------------------------------------------
 void matvec_batch(const std::vector<MvProb>& P, const std::vector<const double2*>& x,
-                  const std::vector<double2*>& y, const Ctx& c) {
+                  const std::vector<double2*>& y, const Ctx& c, bool accumulate) {
   const int n = (int)P.size();
   if (n == 0) return;
   if (n > MAXB) fail(TDVP_EINVAL, "batch too large");
+  if (accumulate && c.prec != TDVP_FP64) fail(TDVP_EINVAL, "accumulating H_eff products are FP64 only");
   if (c.prec == TDVP_FP64) {
     ZGemmBatch g1{};
     WStageBatch<double2> ws{};
@@ -269,6 +270,7 @@ void matvec_batch(const std::vector<MvProb>& P, const std::vector<const double2*
       b.C = y[i];
       b.c_rs = B;
       b.c_cs = 1;
+      b.accumulate = accumulate ? 1 : 0;
     }
     launch_zgemm(g1, c.s);
     launch_wstage(ws, c.s);
@@ -437,7 +439,7 @@ static void env_fp64(int side, const std::vector<EnvProb>& P, const Ctx& c) {
       b.M = B;
       b.N = m * B;
       b.K = A * d;
-      b.A = q.mat;
+      b.A = q.bra ? q.bra : q.mat;
       b.a_rs = 1;
       b.a_cs = B;
       b.conj_a = 1;
@@ -478,7 +480,7 @@ static void env_fp64(int side, const std::vector<EnvProb>& P, const Ctx& c) {
       b.M = A;
       b.N = m * A;
       b.K = d * B;
-      b.A = q.mat;
+      b.A = q.bra ? q.bra : q.mat;
       b.a_rs = (int64_t)d * B;
       b.a_cs = 1;
       b.conj_a = 1;
@@ -489,6 +491,7 @@ static void env_fp64(int side, const std::vector<EnvProb>& P, const Ctx& c) {
       b.c_rs = (int64_t)m * A;
       b.c_cs = 1;
     }
+    b.accumulate = q.accumulate;
   }
   launch_zgemm(g1, c.s);
   launch_wstage(ws, c.s);
@@ -643,6 +646,9 @@ static void env_tc(int side, const std::vector<EnvProb>& P, const Ctx& c) {
 void env_batch(int side, const std::vector<EnvProb>& P, const Ctx& c) {
   if (P.empty()) return;
   if ((int)P.size() > MAXB) fail(TDVP_EINVAL, "batch too large");
+  if (c.prec != TDVP_FP64)
+    for (const auto& q : P)
+      if (q.bra || q.accumulate) fail(TDVP_EINVAL, "mixed bra/ket and accumulating environments are FP64 only");
   if (c.prec == TDVP_FP64) env_fp64(side, P, c);
   else env_tc(side, P, c);
 }

@@ -126,8 +126,11 @@ struct Prec<double2> {
   using AT = double2;
   static constexpr double tol = JACOBI_TOL;
   static constexpr bool dd = false;
-  // pairs whose norms are both below 1e-14 ||theta||_F are rounding noise
-  __device__ static R zero_level(const SvdDesc& P) { return 1e-28 * P.sig[P.n_vec + 1]; }
+  // vectors below 1e-14 ||theta||_F are rounding noise (unless zero_rel says otherwise)
+  __device__ static R zero_level(const SvdDesc& P) {
+    const double zr = P.zero_rel > 0.0 ? P.zero_rel : 1e-28;
+    return fmax(zr * P.sig[P.n_vec + 1], 1e-290);
+  }
   // the FP64 phase tracks the vector norms in sig[0, n_vec) for the tail rule
   static constexpr bool tracks_norms = true;
   __device__ static R wsum(R v) { return warp_sum(v); }

@@ -28,6 +28,9 @@ struct SvdDesc {
   double* V;             // [chi]
   double2* PsiR;         // [chi][cols]
   double* s_sorted;      // [n_vec] all singular values, descending (may be null)
+  double zero_rel;       // FP64 sweeps leave vectors with |x|^2 < zero_rel ||theta||_F^2 alone
+                         // (0: 1e-28, the rounding-noise level; the derivative of a split
+                         // needs every nonzero vector orthogonalised and passes ~1e-250)
 };
 struct SvdBatch {
   int n;

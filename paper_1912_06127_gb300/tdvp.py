@@ -119,6 +119,13 @@ def lib():
         "tdvp_op_heff_noalloc": ([ctypes.c_int] * 5 + [_D, _P, _P, _P, _P, _P], ctypes.c_int),
         "tdvp_profile_read": ([ctypes.c_int, ctypes.c_char_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int64),
                                _D, _D], ctypes.c_int),
+        "tdvp_build_mpo_derivative": ([_P, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+        "tdvp_tangent_create": ([_P, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+        "tdvp_free_tangent": ([_P], None),
+        "tdvp_step_tangent": ([_P, _P, _P, ctypes.POINTER(_P), ctypes.POINTER(StepParams), ctypes.c_int,
+                               ctypes.c_int, ctypes.POINTER(StepStats), _P], ctypes.c_int),
+        "tdvp_measure_tangent": ([_P, _P, ctypes.c_int, _D, _D], ctypes.c_int),
+        "tdvp_gauss_legendre": ([ctypes.c_int, _D, _D], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -327,6 +334,60 @@ def overlap(a: Mps, b: Mps) -> complex:
     out = np.zeros(2)
     _check(lib().tdvp_overlap(a.handle, b.handle, _dptr(out)))
     return complex(out[0], out[1])
+
+
+# ---- derivatives with respect to the model parameters -------------------------
+PARAM_H, PARAM_J = 0, 1
+
+
+def build_mpo_derivative(mpo: Mpo, param: int) -> Mpo:
+    """dW/d(param) of `mpo` (PARAM_H or PARAM_J) as an MPO handle."""
+    h_ = ctypes.c_void_p()
+    _check(lib().tdvp_build_mpo_derivative(mpo.handle, param, ctypes.byref(h_)))
+    d = Mpo(h_)
+    d._base = mpo  # the derivative refers to its MPO
+    return d
+
+
+class Tangent:
+    """Tangent of an MPS in n_dir parameter directions (zero when created)."""
+
+    def __init__(self, mps: Mps, n_dir: int):
+        h_ = ctypes.c_void_p()
+        _check(lib().tdvp_tangent_create(mps.handle, n_dir, ctypes.byref(h_)))
+        self.handle = h_
+        self.mps = mps
+        self.n_dir = n_dir
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tdvp_free_tangent(self.handle)
+            self.handle = None
+
+
+def step_tangent(mps: Mps, mpo: Mpo, tan: Tangent, dmpos: Sequence[Mpo], params: StepParams, n_steps: int = 1,
+                 n_quad: int = 6, stream=None, stats: Optional[StepStats] = None) -> StepStats:
+    st = stats if stats is not None else StepStats()
+    arr = (_P * len(dmpos))(*[d.handle for d in dmpos])
+    _check(lib().tdvp_step_tangent(mps.handle, mpo.handle, tan.handle, arr, ctypes.byref(params), n_quad, n_steps,
+                                   ctypes.byref(st), _stream(stream)))
+    return st
+
+
+def measure_tangent(mps: Mps, tan: Tangent, obs: int = OBS_SZ):
+    """(<O_j> [N], d<O_j> [n_dir, N])."""
+    N, _ = mps.size()
+    val = np.zeros(N, dtype=np.float64)
+    der = np.zeros((tan.n_dir, N), dtype=np.float64)
+    _check(lib().tdvp_measure_tangent(mps.handle, tan.handle, obs, _dptr(val), _dptr(der)))
+    return val, der
+
+
+def gauss_legendre(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    _check(lib().tdvp_gauss_legendre(n, _dptr(x), _dptr(w)))
+    return x, w
 
 
 # ---- kernel-level operations (torch device tensors) -------------------------

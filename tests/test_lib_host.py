@@ -119,3 +119,12 @@ def test_tridiag_expm_degenerate_and_zero_offdiagonal(tdvp):
     c = tdvp.tridiag_expm(a, b, 0.7)
     Tm = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
     assert np.abs(c - scipy.linalg.expm(-0.7j * Tm)[:, 0]).max() < 1e-13
+
+
+def test_gauss_legendre_nodes_match_numpy(tdvp):
+    for n in (1, 2, 5, 8):
+        x, w = tdvp.gauss_legendre(n)
+        z, v = np.polynomial.legendre.leggauss(n)
+        order = np.argsort(x)
+        assert np.allclose(np.sort(x), np.sort(0.5 * (z + 1)), atol=1e-15, rtol=0)
+        assert np.allclose(w[order], 0.5 * v[np.argsort(0.5 * (z + 1))], atol=1e-15, rtol=0)
