@@ -54,6 +54,13 @@ def parse():
     ap.add_argument("--svd-case", type=int, default=0,
                     help="profiling case: two truncated splits of one N x N two-site state "
                          "(half the spectrum kept), no benchmark line")
+    ap.add_argument("--grad-case", action="store_true",
+                    help="the differentiated 41-site Ising quench at chi 64: d<sigma^z_20(t)>/d(h, J) "
+                         "by tdvp_step_tangent, timed, checked against central differences of tdvp_step")
+    ap.add_argument("--grad-steps", type=int, default=4, help="timed steps of --grad-case")
+    ap.add_argument("--grad-init", default="random", choices=["random", "all_up"],
+                    help="--grad-case start: seeded random MPS at chi 64 (every bond saturated, so every "
+                         "step does the full chi = 64 work) or the all-up product state")
     return ap.parse_args()
 
 
@@ -81,6 +88,102 @@ def svd_case(n, prec):
     print(json.dumps({"svd_case": n, "chi": chi, "w": w, "w_expected": w_ref}))
     if chi != n // 2 or abs(w - w_ref) > 1e-9 * float((s ** 2).sum()):
         raise SystemExit("svd case: unexpected truncation")
+
+
+def grad_case(args):
+    """d<sigma^z_20(t)>/d(h, J) of the 41-site long-range Ising chain (alpha = 3,
+    J = h = 1, 6 exponentials, dt = 0.02, chi_max = 64, eps = 1e-12, Lanczos to
+    1e-12 with at most 20 vectors, 6-point quadrature), from a seeded random MPS
+    at chi = 64 (default) or all spins up: one untimed step, then --grad-steps
+    differentiated steps (both directions) timed with CUDA events, the plain
+    FP64 steps timed the same way, and the gradient compared with central
+    differences (step 1e-5) of tdvp_step over the same steps."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_06127_gb300 import tdvp
+    w = I.cfg4_ising_diff()
+    mdl, prm = w.model, w.params
+    site = mdl.N // 2 - 1                      # sigma^z_20 (0-based)
+    kmax, ktol, nq = 20, 1e-12, 6
+    n_steps = args.grad_steps
+    chi = prm.chi_max
+    raw = I.random_mps_tensors(mdl.N, chi, seed=4) if args.grad_init == "random" else None
+    up = I.basis_state("all_up", mdl.N)
+    x, lam = tdvp.fit_power_law(mdl.alpha, mdl.n_exp, mdl.N - 1)
+    stream = torch.cuda.current_stream()
+
+    def params():
+        return tdvp.step_params(prm.dt, chi, eps=prm.eps, krylov_max=kmax, krylov_tol=ktol)
+
+    def initial():
+        return tdvp.init_mps_tensors(raw, chi, 1e-14) if raw is not None else tdvp.init_mps(mdl.N, up, chi)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    def plain(J, h, n):
+        mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, J, h, mdl.n_exp, x, lam)
+        mps = initial()
+        tdvp.step(mps, mpo, params(), 1, stream=stream)           # untimed first step
+        _, ms = timed(lambda: tdvp.step(mps, mpo, params(), n, stream=stream))
+        return tdvp.measure(mps, tdvp.OBS_SZ)[site], list(mps.bond_dims()), ms
+
+    def differentiated(n, profile=False):
+        mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp, x, lam)
+        dm = [tdvp.build_mpo_derivative(mpo, tdvp.PARAM_H), tdvp.build_mpo_derivative(mpo, tdvp.PARAM_J)]
+        mps = initial()
+        tan = tdvp.Tangent(mps, 2)
+        tdvp.step_tangent(mps, mpo, tan, dm, params(), 1, n_quad=nq, stream=stream)   # untimed first step
+        if profile:
+            tdvp.profile(True)
+        st, ms = timed(lambda: tdvp.step_tangent(mps, mpo, tan, dm, params(), n, n_quad=nq, stream=stream))
+        prof = tdvp.profile_read() if profile else None
+        tdvp.profile(False)
+        val, der = tdvp.measure_tangent(mps, tan, tdvp.OBS_SZ)
+        return val[site], der[:, site], list(mps.bond_dims()), ms, st, prof
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    loss, grad, dims, ms_d, st, prof = differentiated(n_steps, profile=True)
+    clk = clocks.stop()
+    loss_p, dims_p, ms_p = plain(mdl.J, mdl.h, n_steps)
+    d = 1e-5
+    fd, same = [], dims_p == dims
+    for dh, dJ in ((d, 0.0), (0.0, d)):
+        a, da, _ = plain(mdl.J + dJ, mdl.h + dh, n_steps)
+        b, db, _ = plain(mdl.J - dJ, mdl.h - dh, n_steps)
+        same = same and da == dims and db == dims
+        fd.append((a - b) / (2 * d))
+    fd = np.array(fd)
+    rel = float(np.abs(grad - fd).max() / max(np.abs(fd).max(), 1e-300))
+    ms_total = sum(v["ms"] for v in prof.values()) if prof else 0.0
+    dom = max(prof, key=lambda k: prof[k]["ms"]) if prof else None
+    line = {
+        "metric": "differentiated TDVP time-steps/s (d<sigma^z_20(t)>/d(h, J), both directions)",
+        "value": n_steps / (ms_d * 1e-3), "unit": "time-steps/s", "n_gpus": 1, "steps": n_steps,
+        "warmup": 1, "ms_per_step": ms_d / n_steps, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "N": mdl.N, "alpha": mdl.alpha, "J": mdl.J, "h": mdl.h, "m": mdl.m,
+                   "chi_max": chi, "dt": prm.dt, "eps": prm.eps, "krylov": [kmax, ktol], "n_quad": nq,
+                   "init": ("seeded random MPS at chi %d (seed 4)" % chi) if raw is not None else "all up",
+                   "observable": "sigma^z_%d (1-based %d)" % (site, site + 1)},
+        "loss": float(loss), "grad_h_J": [float(v) for v in grad], "fd_h_J": [float(v) for v in fd],
+        "grad_rel_err_vs_fd": rel, "fd_step": d, "same_bond_dims_in_fd_runs": bool(same),
+        "loss_plain_run": float(loss_p), "plain_fp64_steps_per_s": n_steps / (ms_p * 1e-3),
+        "cost_vs_plain": ms_d / ms_p, "chi_max_seen": int(max(dims)), "gpu_launches": int(st.kernel_launches),
+        "clocks": clk,
+        "kernels": {k: {"ms": v["ms"], "launches": v["launches"], "share": v["ms"] / max(ms_total, 1e-9)}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]} if prof else None,
+        "dominant_kernel": dom,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def workload(args):
@@ -469,6 +572,9 @@ def main():
     args = parse()
     if args.svd_case:
         svd_case(args.svd_case, PREC[args.precision])
+        return
+    if args.grad_case:
+        grad_case(args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
