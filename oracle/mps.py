@@ -167,9 +167,49 @@ def overlap(a: MPS, b: MPS) -> complex:
     return complex(E[0, 0])
 
 
+def apply_site_op(mps: MPS, op: np.ndarray, j: int) -> MPS:
+    """O_j |psi> with O acting on the physical index of Psi_j (the excitation
+    sigma^z_k |psi_0> of the dynamical correlation function, Sec. IV). A unitary O
+    keeps the inverse canonical gauge."""
+    out = mps.copy()
+    out.Psi[j] = np.einsum("st,atb->asb", op, mps.Psi[j])
+    return out
+
+
+def mixed_local(a: MPS, b: MPS, op: np.ndarray) -> np.ndarray:
+    """<a|O_j|b> for every site j (complex, not normalised), by transfer
+    matrices with a in the bra and b in the ket."""
+    Ma, Mb = a.matrices(), b.matrices()
+    N = len(Ma)
+    L = [np.ones((1, 1), dtype=np.complex128)]
+    for A, B in zip(Ma, Mb):
+        L.append(np.einsum("asb,ax,xsy->by", A.conj(), L[-1], B))
+    R = [None] * (N + 1)
+    R[N] = np.ones((1, 1), dtype=np.complex128)
+    for j in range(N - 1, -1, -1):
+        R[j] = np.einsum("asb,by,xsy->ax", Ma[j].conj(), R[j + 1], Mb[j])
+    return np.array([np.einsum("asb,ax,st,xty,by->", Ma[j].conj(), L[j], op, Mb[j], R[j + 1])
+                     for j in range(N)])
+
+
 def infidelity(a: MPS, b: MPS) -> float:
     """I = 1 - |<a|b>| / sqrt(<a|a><b|b>) (Eq. 24)."""
     return 1.0 - abs(overlap(a, b)) / np.sqrt(norm2(a) * norm2(b))
+
+
+def from_dense(v: np.ndarray, N: int, chi_max: int, d: int = 2) -> MPS:
+    """A state vector (site 0 most significant) as an MPS in the inverse canonical
+    gauge: exact left-to-right SVD factorisation into raw tensors, then canonicalize."""
+    raw = []
+    rest = np.asarray(v, dtype=np.complex128).reshape(1, -1)
+    for j in range(N - 1):
+        a = rest.shape[0]
+        U, s, Vh = np.linalg.svd(rest.reshape(a * d, -1), full_matrices=False)
+        k = int(np.count_nonzero(s > 1e-15 * s[0]))
+        raw.append(U[:, :k].reshape(a, d, k))
+        rest = s[:k, None] * Vh[:k]
+    raw.append(rest.reshape(rest.shape[0], d, 1))
+    return canonicalize(raw, chi_max)
 
 
 def to_dense(mps: MPS) -> np.ndarray:

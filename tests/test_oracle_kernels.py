@@ -199,3 +199,18 @@ def test_canonicalize_gives_inverse_canonical_gauge():
         assert np.allclose(A.conj().T @ A, np.eye(A.shape[1]), atol=1e-12)
         assert np.allclose(B @ B.conj().T, np.eye(B.shape[0]), atol=1e-12)
         assert np.all(np.diff(1.0 / mps.V[j]) <= 1e-15)
+
+
+def test_apply_site_op_and_mixed_local_match_dense_vectors():
+    N = 6
+    a = M.canonicalize(I.random_mps_tensors(N, 4, seed=21), 8)
+    b = M.canonicalize(I.random_mps_tensors(N, 3, seed=22), 8)
+    va, vb = M.to_dense(a), M.to_dense(b)
+    for op in (models.SZ, models.SX, models.SY):
+        got = M.mixed_local(a, b, op)
+        ref = np.array([np.vdot(va, models.site_operator(op, j, N) @ vb) for j in range(N)])
+        assert np.abs(got - ref).max() < 1e-13
+    c = M.apply_site_op(b, models.SY, 2)
+    assert np.abs(M.to_dense(c) - models.site_operator(models.SY, 2, N) @ vb).max() < 1e-14
+    # a unitary keeps the norm and the gauge (the state stays normalised)
+    assert abs(M.norm2(c) - M.norm2(b)) < 1e-13
