@@ -58,6 +58,10 @@ def parse():
                     help="the differentiated 41-site Ising quench at chi 64: d<sigma^z_20(t)>/d(h, J) "
                          "by tdvp_step_tangent, timed, checked against central differences of tdvp_step")
     ap.add_argument("--grad-steps", type=int, default=4, help="timed steps of --grad-case")
+    ap.add_argument("--xxx-case", action="store_true",
+                    help="time steps of the 201-site 1/r^2 XXX chain (m = 32, chi 256, 16 uneven segments, "
+                         "--precision) from a seeded random MPS at chi 256; no benchmark line")
+    ap.add_argument("--xxx-steps", type=int, default=2)
     ap.add_argument("--grad-init", default="random", choices=["random", "all_up"],
                     help="--grad-case start: seeded random MPS at chi 64 (every bond saturated, so every "
                          "step does the full chi = 64 work) or the all-up product state")
@@ -184,6 +188,46 @@ def grad_case(args):
         "dominant_kernel": dom,
     }
     print(json.dumps(line), flush=True)
+
+
+def xxx_case(args):
+    """Throughput of the 1/r^2 XXX quench's time step (N = 201, alpha = 2, 10
+    exponentials -> m = 32, dt = 0.05, chi_max = 256, 16 uneven segments 65, 12,
+    4 x 12, 12, 64) from a seeded random MPS at chi = 256 (every bond saturated):
+    one untimed step, then --xxx-steps steps timed with CUDA events."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_06127_gb300 import tdvp
+    w = I.cfg5_xxx()
+    mdl, prm = w.model, w.params
+    prec = PREC[args.precision]
+    mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
+    mps = tdvp.init_mps_tensors(I.random_mps_tensors(mdl.N, prm.chi_max, seed=0), prm.chi_max, 1e-14)
+    p = tdvp.step_params(prm.dt, prm.chi_max, w_max=prm.w_max, eps=prm.eps, krylov_max=prm.krylov_max,
+                         krylov_tol=prm.krylov_tol, precision=prec, seg_len=prm.seg_len)
+    stream = torch.cuda.current_stream()
+    tdvp.step(mps, mpo, p, 1, stream=stream)
+    clocks = ClockSampler(0)
+    clocks.start()
+    tdvp.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st = tdvp.step(mps, mpo, p, args.xxx_steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = tdvp.profile_read()
+    tdvp.profile(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    tot = sum(v["ms"] for v in prof.values())
+    print(json.dumps({
+        "xxx_case": w.name, "time_steps_per_s": args.xxx_steps / (ms * 1e-3), "ms_per_step": ms / args.xxx_steps,
+        "steps": args.xxx_steps, "precision": args.precision, "m": mdl.m, "segments": prm.seg_len,
+        "chi_max_seen": st.chi_max_seen, "gpu_launches": int(st.kernel_launches), "clocks": clk,
+        "kernels": {k: {"ms": v["ms"], "share": v["ms"] / max(tot, 1e-9)}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]}}), flush=True)
 
 
 def workload(args):
@@ -575,6 +619,9 @@ def main():
         return
     if args.grad_case:
         grad_case(args)
+        return
+    if args.xxx_case:
+        xxx_case(args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -271,6 +271,20 @@ int tdvp_gauss_legendre(int n, double* x_out, double* w_out);
 
 /* ---- measurement (Sec. IV; excluded from timing as in the paper) ---- */
 
+/* A device copy of `src` (tensors and bond dimensions; environments are rebuilt
+ * on the copy's first step). */
+int tdvp_mps_copy(tdvp_mps src, tdvp_mps* out);
+/* Psi_j <- O Psi_j on the physical index: O_j |psi>, op = d x d complex
+ * [s_out][s_in] (2 d^2 doubles, host). A unitary O (sigma^z for the excitation
+ * sigma^z_k |psi_0> of the dynamical correlation function, Sec. IV) keeps the
+ * inverse canonical gauge that tdvp_step needs. Synchronises. */
+int tdvp_apply_site_op(tdvp_mps mps, int j, const double* op);
+/* <a|O_j|b> for every site j, not normalised: out = 2N doubles (re, im per
+ * site), by transfer matrices with a in the bra and b in the ket. With
+ * |b> = e^{-iHt} sigma^z_k |a>, e^{-i E0 t} out_r is the dynamical correlation
+ * function C(r - k, t) of Sec. IV. Synchronises. */
+int tdvp_expect_mixed(tdvp_mps a, tdvp_mps b, int obs, double* out);
+
 /* <psi|O_j|psi>/<psi|psi> for every site j (N doubles) by full transfer-matrix
  * contraction of Psi_1 V_1 ... Psi_N (exact in any gauge). Synchronises. */
 int tdvp_measure(tdvp_mps mps, int obs, double* out);

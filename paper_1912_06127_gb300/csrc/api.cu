@@ -2206,3 +2206,137 @@ int tdvp_gauss_legendre(int n, double* x_out, double* w_out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// One-site operators and mixed expectations (the dynamical correlation
+// function of Sec. IV: C(r - k, t) = e^{-i E0 t} <psi0| sz_r |psi(t)>,
+// |psi(0)> = sz_k |psi0>)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SiteOp {
+  double2 o[16];  // [s_out][s_in], d <= 4
+};
+
+// Psi[a, s, b] <- sum_t op[s][t] Psi[a, t, b], in place (one thread per (a, b))
+__global__ void site_op_kernel(double2* Psi, int A, int d, int B, const SiteOp op) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)A * B;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(i / B), b = (int)(i % B);
+    double2 in[4], out[4];
+    for (int t = 0; t < d; ++t) in[t] = Psi[((int64_t)a * d + t) * B + b];
+    for (int s = 0; s < d; ++s) {
+      double2 acc = make_double2(0, 0);
+      for (int t = 0; t < d; ++t) acc = zadd(acc, zmul(op.o[s * d + t], in[t]));
+      out[s] = acc;
+    }
+    for (int s = 0; s < d; ++s) Psi[((int64_t)a * d + s) * B + b] = out[s];
+  }
+}
+
+// right transfer with bra a and ket b: out[x][y] = sum conj(Ma[x,s,p]) Mb[y,s,q] E[p][q]
+void transfer_right_mixed(const double2* E, const double2* Ma, const double2* Mb, int Aa, int Ab, int d, int Ba,
+                          int Bb, double2* Y, double2* out, cudaStream_t s) {
+  run1(gemm(Ab * d, Ba, Bb, Mb, Bb, 1, 0, E, 1, Bb, Y, Ba), s);
+  run1(gemm(Aa, Ab, d * Ba, Ma, (int64_t)d * Ba, 1, 1, Y, 1, (int64_t)d * Ba, out, Ab), s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdvp_mps_copy(tdvp_mps src, tdvp_mps* out) {
+  return ok_or_code([&] {
+    if (!src || !out) fail(TDVP_EINVAL, "NULL argument");
+    CUDA_TRY(cudaDeviceSynchronize());
+    tdvp_mps_s* S = new_mps(src->N, src->d, src->chi_cap);
+    std::unique_ptr<tdvp_mps_s, void (*)(tdvp_mps_s*)> guard(S, free_mps);
+    S->dims = src->dims;
+    for (int j = 0; j < S->N; ++j)
+      CUDA_TRY(cudaMemcpy(S->Psi[j], src->Psi[j], sizeof(double2) * src->chiL(j) * src->d * src->chiR(j),
+                          cudaMemcpyDeviceToDevice));
+    for (int j = 0; j + 1 < S->N; ++j)
+      CUDA_TRY(cudaMemcpy(S->V[j], src->V[j], sizeof(double) * src->dims[j], cudaMemcpyDeviceToDevice));
+    *out = guard.release();
+  });
+}
+
+int tdvp_apply_site_op(tdvp_mps mps, int j, const double* op) {
+  return ok_or_code([&] {
+    if (!mps || !op) fail(TDVP_EINVAL, "NULL argument");
+    if (j < 0 || j >= mps->N) fail(TDVP_EINVAL, "site out of range");
+    SiteOp o{};
+    std::memcpy(o.o, op, sizeof(double2) * mps->d * mps->d);
+    CUDA_TRY(cudaDeviceSynchronize());
+    const int A = mps->chiL(j), B = mps->chiR(j);
+    const int grid = (int)std::min<int64_t>(cdiv64((int64_t)A * B, 256), 152 * 8);
+    site_op_kernel<<<std::max(grid, 1), 256>>>(mps->Psi[j], A, mps->d, B, o);
+    LAUNCH_CHECK();
+    ++g_launches;
+    CUDA_TRY(cudaDeviceSynchronize());
+    mps->env_id = 0;  // cached environments belong to the old state
+  });
+}
+
+int tdvp_expect_mixed(tdvp_mps a, tdvp_mps b, int obs, double* out) {
+  return ok_or_code([&] {
+    if (!a || !b || !out) fail(TDVP_EINVAL, "NULL argument");
+    if (a->N != b->N || a->d != b->d) fail(TDVP_EINVAL, "states of different shape");
+    if (a->d != 2) fail(TDVP_EINVAL, "Pauli observables need d = 2");
+    double2 op[4];
+    pauli(obs, op);
+    CUDA_TRY(cudaDeviceSynchronize());
+    cudaStream_t s = 0;
+    const int N = a->N, d = a->d;
+    const int64_t cc = std::max(a->chi_cap, b->chi_cap);
+    const int64_t big = cc * d * cc;
+    MeasureBufs mb;
+    mb.Mj = dalloc<double2>(big);
+    mb.X = dalloc<double2>(big);
+    mb.Y = dalloc<double2>(big);
+    mb.rho = dalloc<double2>((size_t)16 * N);
+    double2* Mb = dalloc<double2>(big);
+    std::unique_ptr<double2, void (*)(double2*)> gM(Mb, [](double2* p) { dfree(p); });
+    mb.EL.resize(N + 1);
+    mb.ER.resize(N);
+    for (int j = 0; j <= N; ++j) {
+      const int64_t ca = j == 0 ? 1 : a->chiR(j - 1), cb = j == 0 ? 1 : b->chiR(j - 1);
+      mb.EL[j] = dalloc<double2>((size_t)ca * cb);
+    }
+    for (int j = 0; j < N; ++j) mb.ER[j] = dalloc<double2>((size_t)a->chiR(j) * b->chiR(j));
+    const double2 one = make_double2(1, 0);
+    CUDA_TRY(cudaMemcpy(mb.EL[0], &one, sizeof(double2), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(mb.ER[N - 1], &one, sizeof(double2), cudaMemcpyHostToDevice));
+    for (int j = 0; j < N; ++j) {
+      site_matrix(a, j, mb.Mj, s);
+      site_matrix(b, j, Mb, s);
+      transfer_left(mb.EL[j], mb.Mj, Mb, a->chiL(j), b->chiL(j), d, a->chiR(j), b->chiR(j), mb.X, mb.EL[j + 1], s);
+    }
+    for (int j = N - 1; j >= 1; --j) {
+      site_matrix(a, j, mb.Mj, s);
+      site_matrix(b, j, Mb, s);
+      transfer_right_mixed(mb.ER[j], mb.Mj, Mb, a->chiL(j), b->chiL(j), d, a->chiR(j), b->chiR(j), mb.Y,
+                           mb.ER[j - 1], s);
+    }
+    for (int j = 0; j < N; ++j) {
+      site_matrix(a, j, mb.Mj, s);
+      site_matrix(b, j, Mb, s);
+      const int Aa = a->chiL(j), Ab = b->chiL(j), Ba = a->chiR(j), Bb = b->chiR(j);
+      // X = EL Mb (Aa x d Bb), Y[(x s)][p] = sum_q X[(x s)][q] ER[p][q]
+      run1(gemm(Aa, d * Bb, Ab, mb.EL[j], Ab, 1, 0, Mb, (int64_t)d * Bb, 1, mb.X, (int64_t)d * Bb), s);
+      run1(gemm(Aa * d, Ba, Bb, mb.X, Bb, 1, 0, mb.ER[j], 1, Bb, mb.Y, Ba), s);
+      rho_kernel<<<d * d, 256, 0, s>>>(mb.Mj, mb.Y, Aa, d, Ba, mb.rho + (size_t)16 * j);
+      LAUNCH_CHECK();
+    }
+    std::vector<double2> rho((size_t)16 * N);
+    CUDA_TRY(cudaMemcpy(rho.data(), mb.rho, sizeof(double2) * rho.size(), cudaMemcpyDeviceToHost));
+    for (int j = 0; j < N; ++j) {
+      double2 v = make_double2(0, 0);
+      for (int k = 0; k < d * d; ++k) v = zadd(v, zmul(rho[(size_t)16 * j + k], op[k]));
+      out[2 * j] = v.x;
+      out[2 * j + 1] = v.y;
+    }
+  });
+}
+
+}  // extern "C"

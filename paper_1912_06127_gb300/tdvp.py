@@ -126,6 +126,9 @@ def lib():
                                ctypes.c_int, ctypes.POINTER(StepStats), _P], ctypes.c_int),
         "tdvp_measure_tangent": ([_P, _P, ctypes.c_int, _D, _D], ctypes.c_int),
         "tdvp_gauss_legendre": ([ctypes.c_int, _D, _D], ctypes.c_int),
+        "tdvp_mps_copy": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
+        "tdvp_apply_site_op": ([_P, ctypes.c_int, _D], ctypes.c_int),
+        "tdvp_expect_mixed": ([_P, _P, ctypes.c_int, _D], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -316,6 +319,26 @@ def measure(mps: Mps, obs: int = OBS_SZ) -> np.ndarray:
     out = np.zeros(N, dtype=np.float64)
     _check(lib().tdvp_measure(mps.handle, obs, _dptr(out)))
     return out
+
+
+def mps_copy(mps: Mps) -> Mps:
+    h_ = ctypes.c_void_p()
+    _check(lib().tdvp_mps_copy(mps.handle, ctypes.byref(h_)))
+    return Mps(h_)
+
+
+def apply_site_op(mps: Mps, j: int, op: np.ndarray) -> None:
+    """O_j |psi> in place (op: d x d complex, [s_out][s_in])."""
+    o = np.ascontiguousarray(op, dtype=np.complex128)
+    _check(lib().tdvp_apply_site_op(mps.handle, j, _dptr(o.view(np.float64))))
+
+
+def expect_mixed(a: Mps, b: Mps, obs: int = OBS_SZ) -> np.ndarray:
+    """<a|O_j|b> for every site (complex, not normalised)."""
+    N, _ = a.size()
+    out = np.zeros(2 * N, dtype=np.float64)
+    _check(lib().tdvp_expect_mixed(a.handle, b.handle, obs, _dptr(out)))
+    return out.view(np.complex128).copy()
 
 
 def norm(mps: Mps) -> float:
