@@ -136,6 +136,17 @@ int tdvp_device_ok(void);
 int tdvp_fit_power_law(double alpha, int n_exp, int r_max, double* x_out, double* lam_out);
 
 /* Build the MPO of a model on the current device. Host arrays are copied. */
+/* Host only. The Levenberg-Marquardt alternative to tdvp_fit_power_law that
+ * the Supplemental Material compares for 1/r^2: real x_k, lam_k minimising the
+ * sum over r = 1..r_max of (w_r e_r)^2, e_r = sum_k x_k lam_k^r - r^-alpha,
+ * w_r = 1 (relative = 0) or r^alpha (relative = 1, the relative error), started
+ * from tdvp_fit_power_law (real parts), stopped as the paper's lsqnonlin options
+ * (1000 iterations, 10000 evaluations, step 1e-6, function 1e-14). If the result
+ * has some |lam_k| >= 1 the start is returned. rms_out (may be NULL): the root
+ * mean square of w_r e_r. Outputs as tdvp_fit_power_law (complex, imaginary 0);
+ * pass them to tdvp_build_mpo through tdvp_model.x / .lam. */
+int tdvp_fit_power_law_lm(double alpha, int n_exp, int r_max, int relative, double* x_out, double* lam_out,
+                          double* rms_out);
 int tdvp_build_mpo(const tdvp_model* model, tdvp_mpo* out);
 /* MPO bond dimension m and physical dimension d. */
 int tdvp_mpo_dims(tdvp_mpo mpo, int* m, int* d);

@@ -76,6 +76,41 @@ def fit_power_law(alpha: float, n_exp: int, r_max: int) -> Tuple[np.ndarray, np.
     return fit_exponentials(r ** (-float(alpha)), n_exp)
 
 
+def fit_exponentials_lm(f: np.ndarray, x0: np.ndarray, lam0: np.ndarray, relative: bool):
+    """Levenberg-Marquardt least squares for real x_k, lam_k in f(r) ~ sum_k x_k lam_k^r
+    (the alternative fit of the Supplemental Material's power-law section, with its
+    lsqnonlin stopping values: step 1e-6, function 1e-14, 10000 evaluations), residuals
+    e_r weighted by 1 or 1/f(r). The minimiser is scipy's MINPACK Levenberg-Marquardt.
+    Returns (x, lam, rms of the weighted residuals)."""
+    import scipy.optimize
+    f = np.asarray(f, dtype=np.float64)
+    r = np.arange(1, len(f) + 1, dtype=np.float64)
+    K = len(x0)
+    w = 1.0 / f if relative else np.ones_like(f)
+
+    def res(p):
+        return w * ((p[None, :K] * p[None, K:] ** r[:, None]).sum(axis=1) - f)
+
+    def jac(p):
+        Jx = p[None, K:] ** r[:, None]
+        Jl = p[None, :K] * r[:, None] * p[None, K:] ** (r[:, None] - 1)
+        return w[:, None] * np.hstack([Jx, Jl])
+
+    p0 = np.concatenate([np.real(x0), np.real(lam0)]).astype(np.float64)
+    out = scipy.optimize.least_squares(res, p0, jac=jac, method="lm", xtol=1e-6, ftol=1e-14, max_nfev=10000)
+    p = out.x
+    if not (np.all(np.abs(p[K:]) < 1) and np.all(p[K:] != 0)) or (res(p) ** 2).sum() > (res(p0) ** 2).sum():
+        p = p0
+    return p[:K].astype(np.complex128), p[K:].astype(np.complex128), float(np.sqrt(np.mean(res(p) ** 2)))
+
+
+def fit_power_law_lm(alpha: float, n_exp: int, r_max: int, relative: bool = True):
+    """Levenberg-Marquardt fit of r^-alpha on r = 1..r_max, started from fit_power_law."""
+    r = np.arange(1, r_max + 1, dtype=np.float64)
+    x0, lam0 = fit_power_law(alpha, n_exp, r_max)
+    return fit_exponentials_lm(r ** (-float(alpha)), x0, lam0, relative)
+
+
 def couplings(x: np.ndarray, lam: np.ndarray, r_max: int) -> np.ndarray:
     """V(r) = sum_k x_k lam_k^r for r = 1..r_max (index r-1)."""
     r = np.arange(1, r_max + 1)

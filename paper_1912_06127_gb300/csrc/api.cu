@@ -788,6 +788,17 @@ int tdvp_fit_power_law(double alpha, int n_exp, int r_max, double* x_out, double
   });
 }
 
+int tdvp_fit_power_law_lm(double alpha, int n_exp, int r_max, int relative, double* x_out, double* lam_out,
+                          double* rms_out) {
+  return ok_or_code([&] {
+    if (!x_out || !lam_out) fail(TDVP_EINVAL, "NULL output");
+    std::vector<double2> x, lam;
+    host_fit_power_law_lm(alpha, n_exp, r_max, relative, x, lam, rms_out);
+    std::memcpy(x_out, x.data(), sizeof(double2) * n_exp);
+    std::memcpy(lam_out, lam.data(), sizeof(double2) * n_exp);
+  });
+}
+
 int tdvp_build_mpo(const tdvp_model* model, tdvp_mpo* out) {
   return ok_or_code([&] {
     if (!model || !out) fail(TDVP_EINVAL, "NULL argument");

@@ -267,6 +267,8 @@ struct LzState {
 // ---------------------------------------------------------------------------
 void host_fit_power_law(double alpha, int n_exp, int r_max, std::vector<double2>& x,
                         std::vector<double2>& lam);
+void host_fit_power_law_lm(double alpha, int n_exp, int r_max, int relative, std::vector<double2>& x,
+                           std::vector<double2>& lam, double* rms);
 // c = exp(-i t T) e_0 for symmetric tridiagonal T (alpha diag, beta off-diag)
 __host__ __device__ int tridiag_expm_e0(int k, const double* alpha, const double* beta, double t,
                                         double2* c, double* work);

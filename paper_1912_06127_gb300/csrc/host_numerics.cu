@@ -237,6 +237,124 @@ void host_fit_power_law(double alpha, int n_exp, int r_max, std::vector<double2>
   }
 }
 
+// Levenberg-Marquardt refinement of the sum-of-exponentials fit (the alternative
+// to the shift-invariance fit that the Supplemental Material compares in its
+// power-law section): real x_k, lam_k minimising sum_r (w_r e_r)^2 with
+// e_r = sum_k x_k lam_k^r - r^-alpha, w_r = 1 (absolute) or r^alpha (relative),
+// r = 1..r_max. Marquardt's damped normal equations (J^T J + mu diag(J^T J)) d =
+// -J^T e, mu divided by 10 after an accepted step and multiplied by 10 after a
+// rejected one; stops after 1000 iterations or 10000 evaluations, when the
+// relative step is below 1e-6 or the relative decrease of the sum of squares
+// below 1e-14 (the stopping values of the Supplemental Material's fit). Starts
+// from the real parts of the shift-invariance fit; returns the start unchanged
+// if the result leaves 0 < |lam| < 1.
+void host_fit_power_law_lm(double alpha, int n_exp, int r_max, int relative, std::vector<double2>& x_out,
+                           std::vector<double2>& lam_out, double* rms_out) {
+  host_fit_power_law(alpha, n_exp, r_max, x_out, lam_out);
+  const int K = n_exp, P = 2 * K, R = r_max;
+  std::vector<double> p(P), f(R), w(R);
+  for (int k = 0; k < K; ++k) {
+    p[k] = x_out[k].x;
+    p[K + k] = lam_out[k].x;
+  }
+  for (int r = 1; r <= R; ++r) {
+    f[r - 1] = std::pow((double)r, -alpha);
+    w[r - 1] = relative ? 1.0 / f[r - 1] : 1.0;
+  }
+  auto residual = [&](const std::vector<double>& q, std::vector<double>& e) {
+    double ss = 0.0;
+    for (int r = 1; r <= R; ++r) {
+      double v = -f[r - 1];
+      for (int k = 0; k < K; ++k) v += q[k] * std::pow(q[K + k], r);
+      e[r - 1] = w[r - 1] * v;
+      ss += e[r - 1] * e[r - 1];
+    }
+    return ss;
+  };
+  std::vector<double> e(R), e2(R), J((size_t)R * P), A((size_t)P * P), g(P), d(P), q(P), Lc((size_t)P * P);
+  double S = residual(p, e);
+  const std::vector<double> p0 = p;
+  const double S0 = S;
+  double mu = 1e-3;
+  int nfev = 1;
+  for (int it = 0; it < 1000 && nfev < 10000; ++it) {
+    for (int r = 1; r <= R; ++r)
+      for (int k = 0; k < K; ++k) {
+        const double lk = p[K + k];
+        J[(size_t)(r - 1) * P + k] = w[r - 1] * std::pow(lk, r);
+        J[(size_t)(r - 1) * P + K + k] = w[r - 1] * p[k] * r * std::pow(lk, r - 1);
+      }
+    for (int i = 0; i < P; ++i) {
+      double gi = 0.0;
+      for (int r = 0; r < R; ++r) gi += J[(size_t)r * P + i] * e[r];
+      g[i] = gi;
+      for (int j = 0; j <= i; ++j) {
+        double a = 0.0;
+        for (int r = 0; r < R; ++r) a += J[(size_t)r * P + i] * J[(size_t)r * P + j];
+        A[(size_t)i * P + j] = A[(size_t)j * P + i] = a;
+      }
+    }
+    bool accepted = false, done = false;
+    while (!accepted && nfev < 10000 && mu < 1e20) {
+      // Cholesky of A + mu diag(A)
+      bool pd = true;
+      for (int i = 0; i < P && pd; ++i)
+        for (int j = 0; j <= i; ++j) {
+          double v = A[(size_t)i * P + j] + (i == j ? mu * std::max(A[(size_t)i * P + i], 1e-300) : 0.0);
+          for (int k = 0; k < j; ++k) v -= Lc[(size_t)i * P + k] * Lc[(size_t)j * P + k];
+          if (i == j) {
+            if (!(v > 0.0)) { pd = false; break; }
+            Lc[(size_t)i * P + i] = std::sqrt(v);
+          } else {
+            Lc[(size_t)i * P + j] = v / Lc[(size_t)j * P + j];
+          }
+        }
+      if (!pd) { mu *= 10.0; continue; }
+      for (int i = 0; i < P; ++i) {  // L y = -g
+        double v = -g[i];
+        for (int k = 0; k < i; ++k) v -= Lc[(size_t)i * P + k] * d[k];
+        d[i] = v / Lc[(size_t)i * P + i];
+      }
+      for (int i = P - 1; i >= 0; --i) {  // L^T d = y
+        double v = d[i];
+        for (int k = i + 1; k < P; ++k) v -= Lc[(size_t)k * P + i] * d[k];
+        d[i] = v / Lc[(size_t)i * P + i];
+      }
+      double dn = 0.0, pn = 0.0;
+      for (int i = 0; i < P; ++i) {
+        q[i] = p[i] + d[i];
+        dn += d[i] * d[i];
+        pn += p[i] * p[i];
+      }
+      const double S2 = residual(q, e2);
+      ++nfev;
+      if (S2 < S) {
+        const double rel = (S - S2) / S;
+        p = q;
+        e = e2;
+        S = S2;
+        mu = std::max(mu / 10.0, 1e-15);
+        accepted = true;
+        if (std::sqrt(dn) < 1e-6 * (std::sqrt(pn) + 1e-6) || rel < 1e-14) done = true;
+      } else {
+        mu *= 10.0;
+      }
+    }
+    if (!accepted || done) break;
+  }
+  bool ok = S <= S0;
+  for (int k = 0; k < K; ++k) ok = ok && std::fabs(p[K + k]) < 1.0 && p[K + k] != 0.0;
+  if (!ok) {
+    p = p0;
+    S = S0;
+  }
+  for (int k = 0; k < K; ++k) {
+    x_out[k] = make_double2(p[k], 0.0);
+    lam_out[k] = make_double2(p[K + k], 0.0);
+  }
+  if (rms_out) *rms_out = std::sqrt(S / R);
+}
+
 __host__ __device__ int tridiag_expm_e0(int k, const double* alpha, const double* beta, double t,
                                         double2* c, double* work) {
   return tridiag_expm_e0_impl(k, alpha, beta, t, c, work);

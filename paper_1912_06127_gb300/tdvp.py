@@ -83,6 +83,8 @@ def lib():
         "tdvp_device_ok": ([], ctypes.c_int),
         "tdvp_fit_power_law": ([ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D], ctypes.c_int),
         "tdvp_build_mpo": ([ctypes.POINTER(Model), ctypes.POINTER(_P)], ctypes.c_int),
+        "tdvp_fit_power_law_lm": ([ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D],
+                                  ctypes.c_int),
         "tdvp_mpo_dims": ([_P, _I, _I], ctypes.c_int),
         "tdvp_mpo_tensor": ([_P, _D, _D, _D], ctypes.c_int),
         "tdvp_free_mpo": ([_P], None),
@@ -187,6 +189,16 @@ def fit_power_law(alpha: float, n_exp: int, r_max: int):
     lam = _cplx_out(n_exp)
     _check(lib().tdvp_fit_power_law(alpha, n_exp, r_max, _dptr(x.view(np.float64)), _dptr(lam.view(np.float64))))
     return x, lam
+
+
+def fit_power_law_lm(alpha: float, n_exp: int, r_max: int, relative: bool = True):
+    """(x, lam, rms) of the Levenberg-Marquardt fit of r^-alpha on r = 1..r_max."""
+    x = _cplx_out(n_exp)
+    lam = _cplx_out(n_exp)
+    rms = ctypes.c_double(0.0)
+    _check(lib().tdvp_fit_power_law_lm(alpha, n_exp, r_max, 1 if relative else 0, _dptr(x.view(np.float64)),
+                                       _dptr(lam.view(np.float64)), ctypes.byref(rms)))
+    return x, lam, rms.value
 
 
 class Mpo:

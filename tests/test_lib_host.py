@@ -128,3 +128,23 @@ def test_gauss_legendre_nodes_match_numpy(tdvp):
         order = np.argsort(x)
         assert np.allclose(np.sort(x), np.sort(0.5 * (z + 1)), atol=1e-15, rtol=0)
         assert np.allclose(w[order], 0.5 * v[np.argsort(0.5 * (z + 1))], atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("alpha,K,R,relative", [(2.0, 9, 200, True), (2.0, 9, 200, False), (3.0, 6, 40, True),
+                                                (1.5, 8, 100, False)])
+def test_lm_fit_matches_oracle(tdvp, alpha, K, R, relative):
+    x, lam, rms = tdvp.fit_power_law_lm(alpha, K, R, relative)
+    _, _, orms = models.fit_power_law_lm(alpha, K, R, relative)
+    r = np.arange(1, R + 1, dtype=float)
+    f = r ** -alpha
+    w = 1 / f if relative else np.ones(R)
+    e = (x[None, :] * lam[None, :] ** r[:, None]).sum(1).real - f
+    assert abs(rms - np.sqrt(np.mean((w * e) ** 2))) < 1e-10 * rms
+    assert np.all(np.abs(lam) < 1) and np.abs(lam.imag).max() == 0.0
+    # the library's plain Marquardt iteration stops (step 1e-6, decrease 1e-14) near the level
+    # MINPACK's scaled trust-region variant reaches: within 0.1 % for the relative residuals,
+    # within 15 % for the badly scaled absolute ones
+    assert rms <= (1.001 if relative else 1.15) * orms
+    x0, l0 = tdvp.fit_power_law(alpha, K, R)
+    e0 = (x0[None, :] * l0[None, :] ** r[:, None]).sum(1).real - f
+    assert rms <= np.sqrt(np.mean((w * e0) ** 2)) + 1e-18

@@ -122,3 +122,35 @@ def single_magnon_matrix(kind, V, N):
         for j in range(N):
             H1[j, j] = E0 - 0.5 * sum(V[abs(j - k) - 1] for k in range(N) if k != j)
     return H1
+
+
+def test_lm_fit_recovers_exact_exponential_sums():
+    r = np.arange(1, 61, dtype=float)
+    x = np.array([0.7, -0.2, 0.05])
+    lam = np.array([0.9, 0.6, 0.3])
+    f = (x[None, :] * lam[None, :] ** r[:, None]).sum(1)
+    for relative in (False, True):
+        xf, lf, rms = models.fit_exponentials_lm(f, x * 1.05, lam * 0.98, relative)
+        assert rms < 1e-11
+        order = np.argsort(-lf.real)
+        assert np.allclose(lf.real[order], lam, atol=1e-8) and np.allclose(xf.real[order], x, atol=1e-8)
+
+
+def test_lm_fit_improves_on_the_shift_invariance_start():
+    # the Supplemental Material's comparison: 1/r^2 on r = 1..200 with 9 exponentials;
+    # the relative least-squares fit holds over a longer distance (smaller relative error)
+    alpha, K, R = 2.0, 9, 200
+    r = np.arange(1, R + 1, dtype=float)
+    f = r ** -alpha
+    x0, l0 = models.fit_power_law(alpha, K, R)
+    e0 = (x0[None, :] * l0[None, :] ** r[:, None]).sum(1).real - f
+    for relative in (False, True):
+        x, lam, rms = models.fit_power_law_lm(alpha, K, R, relative)
+        e = (x[None, :] * lam[None, :] ** r[:, None]).sum(1).real - f
+        w = 1 / f if relative else np.ones(R)
+        assert np.sqrt(np.mean((w * e) ** 2)) <= np.sqrt(np.mean((w * e0) ** 2)) + 1e-18
+        assert abs(rms - np.sqrt(np.mean((w * e) ** 2))) < 1e-15
+        assert np.all(np.abs(lam) < 1)
+    x, lam, _ = models.fit_power_law_lm(alpha, K, R, True)
+    e = (x[None, :] * lam[None, :] ** r[:, None]).sum(1).real - f
+    assert np.abs(e / f).max() < 0.5 * np.abs(e0 / f).max()
