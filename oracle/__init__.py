@@ -17,6 +17,7 @@ Modules
              (Sec. III A/B, App. A/B)
   ed      -- exact diagonalisation of the dense 2^N Hamiltonian
   dmrg    -- two-site DMRG ground states with the same building blocks
+  tdvp1   -- one-site TDVP (Eq. proj1site) and the hybrid two-site -> one-site scheme
   grad    -- d<O_j(t)>/d(h, J) of the sweep: the same steps in PyTorch FP64 CPU
              operations, differentiated by forward-mode automatic differentiation
 

@@ -1,0 +1,67 @@
+"""Pins for the oracle's one-site TDVP (1TDVP) and the hybrid 2TDVP -> 1TDVP scheme.
+
+CPU only. At full bond dimension the one-site projector is the identity, so the
+split steps compose to the exact evolution: 1TDVP must reproduce exact
+diagonalisation. Below full rank the scheme is symplectic at fixed bond
+dimension: norm and energy are conserved (to the Krylov accuracy) and the bond
+dimensions do not change. The hybrid scheme switches once every bond is full.
+"""
+import numpy as np
+
+import tdvp_inputs as I
+from oracle import ed, models
+from oracle import mps as M
+from oracle import tdvp as T
+from oracle import tdvp1 as T1
+from oracle.models import ISING, XY
+
+
+def setup(kind, N, alpha, K, h, chi0, chi, seed):
+    x, lam = models.fit_power_law(alpha, K, N - 1)
+    W = models.build_mpo_site(kind, 1.0, h, x, lam)
+    H = models.dense_hamiltonian(kind, N, 1.0, h, models.couplings(x, lam, N - 1))
+    mps = M.canonicalize(I.random_mps_tensors(N, chi0, seed=seed), chi, 1e-14)
+    return W, H, mps
+
+
+def test_full_rank_one_site_tdvp_is_exact():
+    N = 8
+    W, H, mps = setup(ISING, N, 3.0, 4, 0.7, 16, 16, 3)
+    v0 = M.to_dense(mps)
+    eng = T.Engine(mps, W)
+    p = T.Params(dt=0.05, chi_max=16, krylov_max=24, krylov_tol=0.0)
+    T1.step1(eng, p, 6)
+    ref = ed.ExactEvolution(H).evolve(v0, 6 * p.dt)
+    for op in (models.SZ, models.SX):
+        got = M.expect_local(eng.mps, op)
+        want = np.array([np.vdot(ref, models.site_operator(op, j, N) @ ref).real for j in range(N)])
+        assert np.abs(got - want).max() < 1e-9
+    assert abs(M.infidelity(eng.mps, M.from_dense(ref, N, 16))) < 1e-10
+
+
+def test_one_site_tdvp_conserves_norm_energy_and_bond_dimensions():
+    for kind, h in ((ISING, 0.6), (XY, 0.2)):
+        W, H, mps = setup(kind, 10, 2.0, 4, h, 4, 4, 7)
+        dims = mps.bond_dims()
+        assert max(dims) == 4 and dims != [min(2 ** (j + 1), 2 ** (9 - j)) for j in range(9)]
+        eng = T.Engine(mps, W)
+        E0 = M.energy(eng.mps, W)
+        p = T.Params(dt=0.05, chi_max=4, krylov_max=24, krylov_tol=0.0)
+        T1.step1(eng, p, 8)
+        assert eng.mps.bond_dims() == dims
+        assert abs(M.norm2(eng.mps) - 1.0) < 1e-12
+        assert abs(M.energy(eng.mps, W) - E0) < 1e-10 * max(1.0, abs(E0))
+
+
+def test_hybrid_switches_when_bonds_saturate():
+    N = 8
+    x, lam = models.fit_power_law(3.0, 4, N - 1)
+    W = models.build_mpo_site(ISING, 1.0, 1.0, x, lam)
+    eng = T.Engine(M.product_state(I.basis_state("all_up", N)), W)
+    p = T.Params(dt=0.05, chi_max=4, krylov_max=24, krylov_tol=0.0)
+    E0 = M.energy(eng.mps, W)
+    n1 = T1.step_hybrid(eng, p, 12)
+    assert 0 < n1 < 12
+    assert T1.saturated(eng, 4)
+    assert abs(M.norm2(eng.mps) - 1.0) < 1e-10
+    assert abs(M.energy(eng.mps, W) - E0) < 1e-3 * abs(E0)
