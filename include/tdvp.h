@@ -199,6 +199,24 @@ void tdvp_free_mps(tdvp_mps mps);
 int tdvp_step(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps,
               tdvp_step_stats* stats, void* stream);
 
+/* One-site TDVP (Sec. II, Eq. proj1site; the paper's discussion proposes its
+ * parallel form and the hybrid scheme below): n_steps symmetric steps of the
+ * serial sweep at fixed bond dimension -- left to right, each site evolved
+ * forward by dt/2 with H1_eff, then split ((chi_{j-1} d) x chi_j SVD, no
+ * truncation) and its bond matrix evolved backward by dt/2 with the bond term
+ * H0_eff C = sum beta_{j+1}[a,w,a'] C[a',b'] gamma_j[b,w,b'], re-diagonalised (the
+ * inverse canonical gauge restored) and moved into site j+1; the last site
+ * forward by dt; then the mirror sweep, ending with site 0 forward by dt/2.
+ * FP64 only, n_seg <= 1 (TDVP_EINVAL otherwise). Norm and energy are conserved
+ * to the Lanczos accuracy. stats->n_back1 counts the site updates. */
+int tdvp_step1(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps,
+               tdvp_step_stats* stats, void* stream);
+/* The hybrid scheme: per step, a tdvp_step (two-site, any segmentation) while
+ * some bond is below min(chi_max, its largest possible dimension), else a
+ * tdvp_step1. FP64 only. Returns the number of one-site steps (>= 0) or an error. */
+int tdvp_step_hybrid(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps,
+                     tdvp_step_stats* stats, void* stream);
+
 /* ---- ground states: two-site DMRG ----
  * The paper prepares its initial states with two-site DMRG (Sec. IV and the
  * Supplemental Material) and notes that a TDVP time step has the sweep

@@ -40,6 +40,7 @@ struct tdvp_mpo_s {
   std::vector<double2> W;    // [m][m][d][d]
   std::vector<double2> W12;  // [m][m][d^2][d^2]
   DeviceWOp w1, w1t, w2;     // one-site (out right), one-site (out left), two-site
+  DeviceWOp w0;              // the bond (zero-site) term: identity over w, physical dimension 1
   uint64_t id = 0;
   uint64_t base_id = 0;      // derivative MPOs: id of the MPO they differentiate
   int param = -1;            // derivative MPOs: TDVP_PARAM_H or TDVP_PARAM_J
@@ -67,6 +68,9 @@ struct tdvp_mps_s {
   int* d_flag = nullptr;
   int* h_pinned = nullptr;  // [0] = flag, [1] = status, [2..2+MAXB) chi
   double* h_w = nullptr;
+  // one-site sweeps: split factors and a staging buffer (chi_cap^2 d^2 each), two bond vectors
+  double2* w1s[4] = {};
+  double* w1v[2] = {};
 
   int chiL(int j) const { return j == 0 ? 1 : dims[j - 1]; }
   int chiR(int j) const { return j == N - 1 ? 1 : dims[j]; }
@@ -614,6 +618,8 @@ void free_mps(tdvp_mps_s* S) {
   dfree(S->d_flag);
   if (S->h_pinned) cudaFreeHost(S->h_pinned);
   if (S->h_w) cudaFreeHost(S->h_w);
+  for (auto p : S->w1s) dfree(p);
+  for (auto p : S->w1v) dfree(p);
   delete S;
 }
 
@@ -2348,6 +2354,234 @@ int tdvp_expect_mixed(tdvp_mps a, tdvp_mps b, int obs, double* out) {
       out[2 * j + 1] = v.y;
     }
   });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// One-site TDVP (Eq. proj1site: site terms forward, bond terms backward, fixed
+// bond dimension) and the hybrid two-site -> one-site scheme of the paper's
+// discussion, serial sweep, FP64
+// ---------------------------------------------------------------------------
+namespace {
+
+void ensure_w0(tdvp_mpo_s* M) {
+  if (M->w0.m == M->m && M->w0.col_ptr) return;
+  std::vector<double2> I((size_t)M->m * M->m, make_double2(0, 0));
+  for (int w = 0; w < M->m; ++w) I[(size_t)w * M->m + w] = make_double2(1, 0);
+  M->w0.build(I, M->m, 1, false);
+}
+
+void ensure_w1s(tdvp_mps_s* S) {
+  if (S->w1s[0]) return;
+  const int64_t v = (int64_t)S->chi_cap * S->chi_cap * S->d * S->d;
+  for (auto& p : S->w1s) p = dalloc<double2>((size_t)v);
+  for (auto& p : S->w1v) p = dalloc<double>((size_t)S->chi_cap * S->d);
+}
+
+void zgemm1(int Mm, int Nn, int Kk, const double2* A, int64_t lda, const double* kscale, const double2* B,
+            int64_t ldb, double2* C, int64_t ldc, cudaStream_t s) {
+  ZGemmBatch g{};
+  g.n = 1;
+  ZGemmDesc& z = g.d[0];
+  z = ZGemmDesc{};
+  z.M = Mm;
+  z.N = Nn;
+  z.K = Kk;
+  z.A = A;
+  z.a_rs = lda;
+  z.a_cs = 1;
+  z.kscale = kscale;
+  z.B = B;
+  z.b_rs = ldb;
+  z.b_cs = 1;
+  z.C = C;
+  z.c_rs = ldc;
+  z.c_cs = 1;
+  launch_zgemm(g, s, "one_site_zgemm");
+}
+
+void site_forward(tdvp_mps_s* S, tdvp_mpo_s* M, int j, double t, const tdvp_step_params* p, tdvp_step_stats* st,
+                  cudaStream_t s) {
+  Slot* sl = slot_for(S, 0, M->m, p->krylov_max);
+  const int A = S->chiL(j), B = S->chiR(j);
+  MvProb P = make_mv(S, M, A, B, S->d, j, j, false, sl, TDVP_FP64);
+  expm_batch({P}, {S->Psi[j]}, {S->Psi[j]}, {t}, p->krylov_max, p->krylov_tol, Ctx{s, S->d_status, TDVP_FP64});
+  if (st) {
+    st->heff_flops += p->krylov_max * heff_flops(A, B, S->d, M->m, M->w1.nnz);
+    st->n_back1 += 1;
+  }
+}
+
+// zero-site effective Hamiltonian on the bond matrix C [A][B]: L = env [A][m][A], R = env [B][m][B]
+void bond_expm(tdvp_mps_s* S, tdvp_mpo_s* M, const double2* L, const double2* R, int A, int B, double2* C,
+               double t, const tdvp_step_params* p, cudaStream_t s) {
+  Slot* sl = slot_for(S, 0, M->m, p->krylov_max);
+  MvProb P{};
+  P.A = A;
+  P.B = B;
+  P.D = 1;
+  P.m = M->m;
+  P.L = L;
+  P.R = R;
+  P.W = M->w0.op();
+  P.slot = sl;
+  expm_batch({P}, {C}, {C}, {t}, p->krylov_max, p->krylov_tol, Ctx{s, S->d_status, TDVP_FP64});
+}
+
+void left_env(tdvp_mps_s* S, tdvp_mpo_s* M, int j, cudaStream_t s) {  // beta_{j+1} from Psi_j V_j
+  Slot* sl = slot_for(S, 0, M->m, 1);
+  ScaleBatch sb{};
+  sb.n = 1;
+  sb.d[0] = ScaleDesc{S->Psi[j], sl->Amat, S->V[j], S->chiL(j), S->d, S->chiR(j), 0, nullptr, nullptr};
+  launch_scale_bond(sb, s);
+  env_batch(0, {EnvProb{S->chiL(j), S->chiR(j), S->d, M->m, S->beta[j], sl->Amat, S->beta[j + 1], M->w1.op(), sl}},
+            Ctx{s, S->d_status, TDVP_FP64});
+}
+
+void right_env(tdvp_mps_s* S, tdvp_mpo_s* M, int j, cudaStream_t s) {  // gamma_j from V_j Psi_{j+1}
+  Slot* sl = slot_for(S, 0, M->m, 1);
+  ScaleBatch sb{};
+  sb.n = 1;
+  sb.d[0] = ScaleDesc{S->Psi[j + 1], sl->Bmat, S->V[j], S->chiL(j + 1), S->d, S->chiR(j + 1), 1, nullptr, nullptr};
+  launch_scale_bond(sb, s);
+  env_batch(1, {EnvProb{S->chiL(j + 1), S->chiR(j + 1), S->d, M->m, S->gamma[j + 1], sl->Bmat, S->gamma[j],
+                        M->w1t.op(), sl}},
+            Ctx{s, S->d_status, TDVP_FP64});
+}
+
+// split site j as (chi_{j-1} d) x chi_j, evolve the bond matrix of bond j backward
+// by tau, move it into site j + 1 (the inverse canonical gauge restored on bond j)
+void bond_backward_right(tdvp_mps_s* S, tdvp_mpo_s* M, int j, double tau, const tdvp_step_params* p,
+                         cudaStream_t s) {
+  const int A = S->chiL(j), d = S->d, b = S->dims[j], Bn = S->chiR(j + 1);
+  Slot* sl = slot_for(S, 0, M->m, p->krylov_max);
+  double2 *P1 = S->w1s[0], *R1 = S->w1s[1], *P2 = S->w1s[2], *Tm = S->w1s[3];
+  double *V1 = S->w1v[0], *V2 = S->w1v[1];
+  const int k = device_split(S, sl, S->Psi[j], A * d, b, std::min(A * d, b), 0.0, 0.0, P1, V1, R1, nullptr,
+                             nullptr, s);
+  // beta_{j+1} from A_j = U = P1 V1
+  ScaleBatch sb{};
+  sb.n = 1;
+  sb.d[0] = ScaleDesc{P1, sl->Amat, V1, A, d, k, 0, nullptr, nullptr};
+  launch_scale_bond(sb, s);
+  env_batch(0, {EnvProb{A, k, d, M->m, S->beta[j], sl->Amat, S->beta[j + 1], M->w1.op(), sl}},
+            Ctx{s, S->d_status, TDVP_FP64});
+  bond_expm(S, M, S->beta[j + 1], S->gamma[j], k, b, R1, -tau, p, s);
+  // R1 (k x b) -> P2 = u s, V2 = 1/s, R2 = s v^H (into P1's successor buffer Tm)
+  double2* R2 = Tm;
+  const int k2 = device_split(S, sl, R1, k, b, std::min(k, b), 0.0, 0.0, P2, V2, R2, nullptr, nullptr, s);
+  // Psi_{j+1} <- R2 V_j(old) Psi_{j+1}: staged through R1 (free now)
+  zgemm1(k2, d * Bn, b, R2, b, S->V[j], S->Psi[j + 1], (int64_t)d * Bn, R1, (int64_t)d * Bn, s);
+  CUDA_TRY(cudaMemcpyAsync(S->Psi[j + 1], R1, sizeof(double2) * k2 * d * Bn, cudaMemcpyDeviceToDevice, s));
+  // Psi_j <- U u s = P1 V1 P2
+  zgemm1(A * d, k2, k, P1, k, V1, P2, k2, S->Psi[j], k2, s);
+  CUDA_TRY(cudaMemcpyAsync(S->V[j], V2, sizeof(double) * k2, cudaMemcpyDeviceToDevice, s));
+  S->dims[j] = k2;
+  left_env(S, M, j, s);
+}
+
+// split site j as chi_{j-1} x (d chi_j), evolve the bond matrix of bond j - 1
+// backward by tau, move it into site j - 1
+void bond_backward_left(tdvp_mps_s* S, tdvp_mpo_s* M, int j, double tau, const tdvp_step_params* p,
+                        cudaStream_t s) {
+  const int a = S->dims[j - 1], d = S->d, Bn = S->chiR(j), Al = S->chiL(j - 1);
+  Slot* sl = slot_for(S, 0, M->m, p->krylov_max);
+  double2 *P1 = S->w1s[0], *R1 = S->w1s[1], *P2 = S->w1s[2], *R2 = S->w1s[3];
+  double *V1 = S->w1v[0], *V2 = S->w1v[1];
+  const int k = device_split(S, sl, S->Psi[j], a, d * Bn, std::min(a, d * Bn), 0.0, 0.0, P1, V1, R1, nullptr,
+                             nullptr, s);
+  // gamma_{j-1} from B_j = V1 R1
+  ScaleBatch sb{};
+  sb.n = 1;
+  sb.d[0] = ScaleDesc{R1, sl->Bmat, V1, k, d, Bn, 1, nullptr, nullptr};
+  launch_scale_bond(sb, s);
+  env_batch(1, {EnvProb{k, Bn, d, M->m, S->gamma[j], sl->Bmat, S->gamma[j - 1], M->w1t.op(), sl}},
+            Ctx{s, S->d_status, TDVP_FP64});
+  bond_expm(S, M, S->beta[j], S->gamma[j - 1], a, k, P1, -tau, p, s);
+  // P1 (a x k) -> P2 = u s, V2 = 1/s, R2 = s v^H
+  const int k2 = device_split(S, sl, P1, a, k, std::min(a, k), 0.0, 0.0, P2, V2, R2, nullptr, nullptr, s);
+  // Psi_j <- R2 V1 R1 (k2 x d Bn)
+  zgemm1(k2, d * Bn, k, R2, k, V1, R1, (int64_t)d * Bn, S->Psi[j], (int64_t)d * Bn, s);
+  // Psi_{j-1} <- Psi_{j-1} V_{j-1}(old) P2, staged through R1 (free now)
+  zgemm1(Al * d, k2, a, S->Psi[j - 1], a, S->V[j - 1], P2, k2, R1, k2, s);
+  CUDA_TRY(cudaMemcpyAsync(S->Psi[j - 1], R1, sizeof(double2) * Al * d * k2, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(S->V[j - 1], V2, sizeof(double) * k2, cudaMemcpyDeviceToDevice, s));
+  S->dims[j - 1] = k2;
+  right_env(S, M, j - 1, s);
+}
+
+void step1_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_steps, tdvp_step_stats* st,
+                cudaStream_t s) {
+  check_params(S, M, p);
+  if (p->precision != TDVP_FP64) fail(TDVP_EINVAL, "one-site sweeps are FP64 only");
+  if (p->n_seg > 1) fail(TDVP_EINVAL, "one-site sweeps are serial (n_seg <= 1)");
+  ensure_small_buffers(S);
+  ensure_w0(M);
+  ensure_w1s(S);
+  const int64_t l0 = g_launches;
+  if (S->env_id != M->id) build_all_envs(S, M, s);
+  const int N = S->N;
+  const double tau = 0.5 * p->dt;
+  for (int step = 0; step < n_steps; ++step) {
+    right_env(S, M, 0, s);  // gamma_0 of the current state (a two-site half leaves it behind)
+    for (int j = 0; j + 1 < N; ++j) {
+      site_forward(S, M, j, tau, p, st, s);
+      bond_backward_right(S, M, j, tau, p, s);
+    }
+    site_forward(S, M, N - 1, 2 * tau, p, st, s);
+    for (int j = N - 1; j >= 1; --j) {
+      bond_backward_left(S, M, j, tau, p, s);
+      site_forward(S, M, j - 1, tau, p, st, s);
+    }
+    read_stage_results(S, 0, s);
+    if (st) st->n_stages += 4 * N - 2;
+  }
+  // tensor-core operand forms of the environments are stale now
+  S->beta32_ok.assign(N, 0);
+  S->gamma32_ok.assign(N, 0);
+  if (st) st->kernel_launches += g_launches - l0;
+}
+
+bool bonds_saturated(const tdvp_mps_s* S, int chi_max) {
+  for (int j = 0; j + 1 < S->N; ++j)
+    if (S->dims[j] < std::min(chi_max, S->cap[j])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdvp_step1(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps, tdvp_step_stats* stats,
+               void* stream) {
+  return ok_or_code([&] {
+    if (!mps || !mpo) fail(TDVP_EINVAL, "NULL handle");
+    if (n_steps < 0) fail(TDVP_EINVAL, "n_steps < 0");
+    step1_impl(mps, mpo, params, n_steps, stats, (cudaStream_t)stream);
+  });
+}
+
+int tdvp_step_hybrid(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps,
+                     tdvp_step_stats* stats, void* stream) {
+  int n1 = 0;
+  const int rc = ok_or_code([&] {
+    if (!mps || !mpo || !params) fail(TDVP_EINVAL, "NULL argument");
+    if (n_steps < 0) fail(TDVP_EINVAL, "n_steps < 0");
+    if (params->precision != TDVP_FP64) fail(TDVP_EINVAL, "the hybrid scheme is FP64 only");
+    tdvp_step_params serial = *params;  // the one-site sweep is serial
+    serial.n_seg = 0;
+    serial.seg_len = nullptr;
+    for (int i = 0; i < n_steps; ++i) {
+      if (bonds_saturated(mps, params->chi_max)) {
+        step1_impl(mps, mpo, &serial, 1, stats, (cudaStream_t)stream);
+        ++n1;
+      } else {
+        step_impl(mps, mpo, params, 1, stats, (cudaStream_t)stream);
+      }
+    }
+  });
+  return rc == TDVP_OK ? n1 : rc;
 }
 
 }  // extern "C"

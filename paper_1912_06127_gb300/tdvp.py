@@ -99,6 +99,10 @@ def lib():
         "tdvp_step": ([_P, _P, ctypes.POINTER(StepParams), ctypes.c_int, ctypes.POINTER(StepStats), _P],
                       ctypes.c_int),
         "tdvp_measure": ([_P, ctypes.c_int, _D], ctypes.c_int),
+        "tdvp_step1": ([_P, _P, ctypes.POINTER(StepParams), ctypes.c_int, ctypes.POINTER(StepStats), _P],
+                       ctypes.c_int),
+        "tdvp_step_hybrid": ([_P, _P, ctypes.POINTER(StepParams), ctypes.c_int, ctypes.POINTER(StepStats), _P],
+                             ctypes.c_int),
         "tdvp_reorthonormalize": ([_P, ctypes.c_double], ctypes.c_int),
         "tdvp_dmrg": ([_P, _P, ctypes.POINTER(DmrgParams), ctypes.c_int, ctypes.POINTER(DmrgStats), _P],
                       ctypes.c_int),
@@ -308,6 +312,23 @@ def step(mps: Mps, mpo: Mpo, params: StepParams, n_steps: int = 1, stream=None,
     _check(lib().tdvp_step(mps.handle, mpo.handle, ctypes.byref(params), n_steps, ctypes.byref(st),
                            _stream(stream)))
     return st
+
+
+def step1(mps: Mps, mpo: Mpo, params: StepParams, n_steps: int = 1, stream=None,
+          stats: Optional[StepStats] = None) -> StepStats:
+    """One-site TDVP steps (serial, FP64, fixed bond dimension)."""
+    st = stats if stats is not None else StepStats()
+    _check(lib().tdvp_step1(mps.handle, mpo.handle, ctypes.byref(params), n_steps, ctypes.byref(st),
+                            _stream(stream)))
+    return st
+
+
+def step_hybrid(mps: Mps, mpo: Mpo, params: StepParams, n_steps: int = 1, stream=None,
+                stats: Optional[StepStats] = None) -> int:
+    """Two-site steps until every bond is full, then one-site steps; returns the one-site count."""
+    st = stats if stats is not None else StepStats()
+    return _check(lib().tdvp_step_hybrid(mps.handle, mpo.handle, ctypes.byref(params), n_steps, ctypes.byref(st),
+                                         _stream(stream)))
 
 
 def dmrg_params(chi_max: int, w_max: float = 0.0, eps: float = 1e-12, krylov_max: int = 8,
