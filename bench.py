@@ -106,7 +106,7 @@ def grad_case(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1912_06127_gb300 import tdvp
-    w = I.cfg4_ising_diff()
+    w = I.tfim_n41_derivative()
     mdl, prm = w.model, w.params
     site = mdl.N // 2 - 1                      # sigma^z_20 (0-based)
     kmax, ktol, nq = 20, 1e-12, 6
@@ -199,7 +199,7 @@ def xxx_case(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1912_06127_gb300 import tdvp
-    w = I.cfg5_xxx()
+    w = I.xxx_n201_quench()
     mdl, prm = w.model, w.params
     prec = PREC[args.precision]
     mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
@@ -231,7 +231,7 @@ def xxx_case(args):
 
 
 def workload(args):
-    w = I.cfg3_ising_large(PREC[args.precision])
+    w = I.tfim_n101_quench(PREC[args.precision])
     return w
 
 
@@ -414,7 +414,7 @@ def cpu_baseline_sample(chi, seconds_budget=30.0):
     step time, i.e. an upper bound on its steps/s)."""
     from oracle import models
     from oracle import tdvp as T
-    w = I.cfg3_ising_large()
+    w = I.tfim_n101_quench()
     mdl = w.model
     x, lam = models.fit_power_law(mdl.alpha, mdl.n_exp, mdl.N - 1)
     W = models.build_mpo_site(mdl.kind, mdl.J, mdl.h, x, lam)

@@ -141,7 +141,7 @@ def even_partition(N: int, p: int) -> List[int]:
 # (Supplemental Material, partition tables) where the sizes match.
 # ---------------------------------------------------------------------------
 
-def cfg1_ising_small() -> Workload:
+def tfim_n10_quench() -> Workload:
     """Long-range TFIM, N=10, alpha=3, J=1, h=1, 4 exponentials (m=6), all up,
     dt=0.01 x 100, chi_max=32 (no truncation), one segment, FP64."""
     return Workload(
@@ -151,7 +151,7 @@ def cfg1_ising_small() -> Workload:
         n_steps=100, init="all_up")
 
 
-def cfg2_xy_medium() -> Workload:
+def xy_n51_quench() -> Workload:
     """Long-range XY, N=51, alpha=1.5, 6 exponentials (m=14), Neel start,
     dt=0.02 x 200, chi_max=128, relative cutoff 1e-10, 4 segments 13/13/13/12."""
     return Workload(
@@ -161,7 +161,7 @@ def cfg2_xy_medium() -> Workload:
         n_steps=200, init="neel")
 
 
-def cfg3_ising_large(precision: int = TF32X3) -> Workload:
+def tfim_n101_quench(precision: int = TF32X3) -> Workload:
     """Long-range TFIM, N=101, alpha=1.5, J=1, h=0.5, 8 exponentials (m=10),
     dt=0.01, chi_max=256, 8 segments 15 / 12 x 6 / 14 (the paper's 101-site
     partition), contractions in TF32 / 3xTF32 or FP64."""
@@ -173,7 +173,7 @@ def cfg3_ising_large(precision: int = TF32X3) -> Workload:
         n_steps=300, init="all_up")
 
 
-def cfg4_ising_diff() -> Workload:
+def tfim_n41_derivative() -> Workload:
     return Workload(
         name="tfim_n41_a3_m8_chi64_p1",
         model=Model(ISING, 41, 3.0, 1.0, 1.0, 6),
@@ -181,7 +181,7 @@ def cfg4_ising_diff() -> Workload:
         n_steps=100, init="all_up")
 
 
-def cfg5_xxx() -> Workload:
+def xxx_n201_quench() -> Workload:
     return Workload(
         name="xxx_n201_a2_m32_chi256_p16",
         model=Model(XXX, 201, 2.0, 1.0, 0.0, 10),

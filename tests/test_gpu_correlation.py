@@ -1,5 +1,5 @@
-"""GPU parity of the pieces of the dynamical correlation function (config 5's
-quantity): one-site operator application, MPS copy and mixed expectations
+"""GPU parity of the pieces of the dynamical correlation function of the 1/r^2
+XXX quench: one-site operator application, MPS copy and mixed expectations
 <a|O_j|b> against the oracle; and C(r - k, t) = e^{-i E0 t} <psi0|sz_r|psi(t)>
 of the 1/r^2 XXX chain from a GPU DMRG ground state, against the oracle's run
 of the same DMRG and sweep (1e-8) and against exact diagonalisation (1e-6,

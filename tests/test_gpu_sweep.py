@@ -49,8 +49,8 @@ def compare(tdvp, mps, mpo, eng, W, tol):
     assert abs(tdvp.energy(mps, mpo) - M.energy(eng.mps, W)) < tol * max(1.0, abs(M.energy(eng.mps, W)))
 
 
-def test_sweep_serial_cfg1_fp64():
-    w = I.cfg1_ising_small()
+def test_sweep_serial_tfim_n10_fp64():
+    w = I.tfim_n10_quench()
     m = w.model
     tdvp, mps, mpo, eng, W, st = run_pair(m.kind, m.N, m.alpha, m.J, m.h, m.n_exp,
                                           I.basis_state("all_up", m.N), 0.01, 20, 32)
@@ -61,8 +61,8 @@ def test_sweep_serial_cfg1_fp64():
 
 
 @pytest.mark.parametrize("seg", [[5, 5], [2, 3, 3, 2], [3, 3, 4]])
-def test_sweep_segments_cfg1_fp64(seg):
-    w = I.cfg1_ising_small()
+def test_sweep_segments_tfim_n10_fp64(seg):
+    w = I.tfim_n10_quench()
     m = w.model
     tdvp, mps, mpo, eng, W, st = run_pair(m.kind, m.N, m.alpha, m.J, m.h, m.n_exp,
                                           I.basis_state("all_up", m.N), 0.01, 10, 32, seg=seg)
@@ -107,7 +107,7 @@ def test_sweep_single_magnon_merge_off():
 
 def test_sweep_production_krylov():
     # the paper's Lanczos settings: at most 8 vectors, tolerance 1e-6
-    w = I.cfg1_ising_small()
+    w = I.tfim_n10_quench()
     m = w.model
     tdvp, mps, mpo, eng, W, st = run_pair(m.kind, m.N, m.alpha, m.J, m.h, m.n_exp,
                                           I.basis_state("all_up", m.N), 0.01, 10, 32, kmax=8, tol=1e-6)
@@ -116,7 +116,7 @@ def test_sweep_production_krylov():
 
 @pytest.mark.parametrize("prec,tol", [(2, 1e-5), (1, 2e-3)], ids=["tf32x3", "tf32"])
 def test_sweep_mixed_precision(prec, tol):
-    w = I.cfg1_ising_small()
+    w = I.tfim_n10_quench()
     m = w.model
     tdvp, mps, mpo, eng, W, st = run_pair(m.kind, m.N, m.alpha, m.J, m.h, m.n_exp,
                                           I.basis_state("all_up", m.N), 0.01, 20, 32, seg=[5, 5], prec=prec)
@@ -171,7 +171,7 @@ def test_full_size_mixed_step_matches_fp64_step():
     relative error of Theta') are compared loosely."""
     torch_or_skip()
     tdvp = lib()
-    w = I.cfg3_ising_large()
+    w = I.tfim_n101_quench()
     mdl, prm = w.model, w.params
     mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
     raw = I.random_mps_tensors(mdl.N, prm.chi_max, seed=0)
@@ -246,14 +246,14 @@ def test_sweep_edge_cases(N, chi, seg):
     assert st.n_fwd2 == eng.stats.n_fwd2 and st.n_back1 == eng.stats.n_back1
 
 
-def test_cfg2_full_size_properties():
-    """Config 2 at its full size (XY, N = 51, chi_max = 128, eps = 1e-10, four
+def test_xy_n51_full_size_properties():
+    """The 51-site XY quench at its full size (XY, N = 51, chi_max = 128, eps = 1e-10, four
     segments 13/13/13/12, Neel start): the XY Hamiltonian conserves the total
     S^z (+1 for the odd chain's Neel state) to rounding; the energy of the TDVP state is conserved up
     to the truncation, and the norm drops by about the discarded weight."""
     torch_or_skip()
     tdvp = lib()
-    w = I.cfg2_xy_medium()
+    w = I.xy_n51_quench()
     mdl, prm = w.model, w.params
     mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
     mps = tdvp.init_mps(mdl.N, I.basis_state("neel", mdl.N), prm.chi_max)

@@ -1,4 +1,4 @@
-"""Pin for the dynamical correlation function of the 1/r^2 XXX chain (config 5's quantity).
+"""Pin for the dynamical correlation function of the 1/r^2 XXX chain (the quantity of the 201-site quench).
 
 CPU only. C(r, t) = e^{-i E0 t} <psi0| sigma^z_r |psi(t)>, |psi(t)> = e^{-iHt} sigma^z_k |psi0>
 (Sec. IV, Eq. of the Haldane-Shastry comparison), from the oracle's sweep at full rank started

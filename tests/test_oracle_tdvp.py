@@ -18,8 +18,8 @@ from oracle.models import ISING, XXX, XY
 from test_oracle_models import single_magnon_matrix
 
 
-def cfg1_setup(N=10):
-    w = I.cfg1_ising_small()
+def tfim_n10_setup(N=10):
+    w = I.tfim_n10_quench()
     mdl = w.model
     x, lam = models.fit_power_law(mdl.alpha, mdl.n_exp, N - 1)
     W = models.build_mpo_site(mdl.kind, mdl.J, mdl.h, x, lam)
@@ -29,7 +29,7 @@ def cfg1_setup(N=10):
 
 def test_serial_matches_ed_full_rank():
     N = 10
-    W, H = cfg1_setup(N)
+    W, H = tfim_n10_setup(N)
     st = I.basis_state("all_up", N)
     eng = T.Engine(M.product_state(st), W)
     p = T.Params(dt=0.01, chi_max=32, krylov_max=10, krylov_tol=0.0)
@@ -49,7 +49,7 @@ def test_serial_matches_ed_full_rank():
 def test_serial_production_krylov_within_1e5():
     # the paper's Lanczos settings (8 vectors, tol 1e-6)
     N = 10
-    W, H = cfg1_setup(N)
+    W, H = tfim_n10_setup(N)
     st = I.basis_state("all_up", N)
     eng = T.Engine(M.product_state(st), W)
     p = T.Params(dt=0.01, chi_max=32)
@@ -172,9 +172,9 @@ def test_boundary_ops_by_left_segment():
                 assert o.kind == "fwd2" and o.j == e and o.env == "LR"
 
 
-def run_cfg1(seg, dt, tf, order="stage", merge=1, chi=32):
+def run_tfim_n10(seg, dt, tf, order="stage", merge=1, chi=32):
     N = 10
-    W, _ = cfg1_setup(N)
+    W, _ = tfim_n10_setup(N)
     eng = T.Engine(M.product_state(I.basis_state("all_up", N)), W)
     p = T.Params(dt=dt, chi_max=chi, krylov_max=10, krylov_tol=0.0, seg_len=seg,
                  merge_turning=merge)
@@ -183,8 +183,8 @@ def run_cfg1(seg, dt, tf, order="stage", merge=1, chi=32):
 
 
 def test_execution_order_independence():
-    a = run_cfg1([2, 3, 3, 2], 0.02, 0.2, order="stage")
-    b = run_cfg1([2, 3, 3, 2], 0.02, 0.2, order="segment")
+    a = run_tfim_n10([2, 3, 3, 2], 0.02, 0.2, order="stage")
+    b = run_tfim_n10([2, 3, 3, 2], 0.02, 0.2, order="segment")
     for x, y in zip(a.mps.Psi, b.mps.Psi):
         assert np.array_equal(x, y)
 
@@ -192,23 +192,23 @@ def test_execution_order_independence():
 def test_segments_close_to_serial_and_improve_with_dt():
     infid = []
     for dt in (0.04, 0.02):
-        s = run_cfg1(None, dt, 0.4)
-        q = run_cfg1([5, 5], dt, 0.4)
+        s = run_tfim_n10(None, dt, 0.4)
+        q = run_tfim_n10([5, 5], dt, 0.4)
         infid.append(M.infidelity(s.mps, q.mps))
     assert infid[0] < 1e-7 and infid[1] < infid[0]
 
 
 def test_merge_off_also_matches_ed():
     N = 10
-    W, H = cfg1_setup(N)
-    eng = run_cfg1([5, 5], 0.01, 0.1, merge=0)
+    W, H = tfim_n10_setup(N)
+    eng = run_tfim_n10([5, 5], 0.01, 0.1, merge=0)
     ref = ed.expect_sz_dense(ed.ExactEvolution(H).evolve(
         ed.product_vector(I.basis_state("all_up", N)), 0.1), N)
     assert np.abs(M.expect_sz(eng.mps) - ref).max() < 1e-8
 
 
 def test_truncated_run_reports_discarded_weight():
-    eng = run_cfg1(None, 0.02, 0.4, chi=4)
+    eng = run_tfim_n10(None, 0.02, 0.4, chi=4)
     assert max(eng.mps.bond_dims()) == 4
     assert eng.stats.w_total > 0
     # no renormalisation: the norm shrinks by about the discarded weight
