@@ -148,3 +148,23 @@ def test_lm_fit_matches_oracle(tdvp, alpha, K, R, relative):
     x0, l0 = tdvp.fit_power_law(alpha, K, R)
     e0 = (x0[None, :] * l0[None, :] ** r[:, None]).sum(1).real - f
     assert rms <= np.sqrt(np.mean((w * e0) ** 2)) + 1e-18
+
+
+def test_new_entry_points_reject_bad_arguments(tdvp):
+    L = tdvp.lib()
+    import ctypes
+    out = ctypes.c_void_p()
+    x = np.zeros(4)
+    assert L.tdvp_gauss_legendre(0, tdvp._dptr(x), tdvp._dptr(x)) == -1
+    assert L.tdvp_fit_power_law_lm(2.0, 0, 10, 1, tdvp._dptr(x), tdvp._dptr(x), None) == -1
+    assert L.tdvp_fit_power_law_lm(2.0, 2, 10, 1, None, None, None) == -1
+    assert L.tdvp_build_mpo_derivative(None, 0, ctypes.byref(out)) == -1
+    assert L.tdvp_tangent_create(None, 2, ctypes.byref(out)) == -1
+    assert L.tdvp_step_tangent(None, None, None, None, None, 6, 1, None, None) == -1
+    assert L.tdvp_measure_tangent(None, None, 0, None, None) == -1
+    assert L.tdvp_step1(None, None, None, 1, None, None) == -1
+    assert L.tdvp_step_hybrid(None, None, None, 1, None, None) == -1
+    assert L.tdvp_mps_copy(None, ctypes.byref(out)) == -1
+    assert L.tdvp_apply_site_op(None, 0, None) == -1
+    assert L.tdvp_expect_mixed(None, None, 0, None) == -1
+    assert "NULL" in tdvp.last_error() or tdvp.last_error()
