@@ -62,6 +62,8 @@ def parse():
                     help="time steps of the 201-site 1/r^2 XXX chain (m = 32, chi 256, 16 uneven segments, "
                          "--precision) from a seeded random MPS at chi 256; no benchmark line")
     ap.add_argument("--xxx-steps", type=int, default=2)
+    ap.add_argument("--tdvp1-case", action="store_true",
+                    help="one-site vs two-site FP64 steps on the 41-site Ising chain at chi 64; no benchmark line")
     ap.add_argument("--grad-init", default="random", choices=["random", "all_up"],
                     help="--grad-case start: seeded random MPS at chi 64 (every bond saturated, so every "
                          "step does the full chi = 64 work) or the all-up product state")
@@ -228,6 +230,43 @@ def xxx_case(args):
         "chi_max_seen": st.chi_max_seen, "gpu_launches": int(st.kernel_launches), "clocks": clk,
         "kernels": {k: {"ms": v["ms"], "share": v["ms"] / max(tot, 1e-9)}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]}}), flush=True)
+
+
+def tdvp1_case(args):
+    """One-site (tdvp_step1) against two-site (tdvp_step) FP64 steps of the 41-site
+    long-range Ising chain (alpha = 3, J = h = 1, 6 exponentials, dt = 0.02,
+    chi = 64, Lanczos <= 8 vectors to 1e-10) from a seeded random MPS at chi = 64
+    (every bond full, the regime where the hybrid scheme switches): one untimed
+    step of each, then one timed step of each (CUDA events); the one-site step's
+    norm and energy change."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_06127_gb300 import tdvp
+    w = I.tfim_n41_derivative()
+    mdl, prm = w.model, w.params
+    chi = prm.chi_max
+    mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
+    raw = I.random_mps_tensors(mdl.N, chi, seed=4)
+    p = tdvp.step_params(prm.dt, chi, eps=prm.eps, krylov_max=8, krylov_tol=1e-10)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, fn in (("two_site", tdvp.step), ("one_site", tdvp.step1)):
+        mps = tdvp.init_mps_tensors(raw, chi, 1e-14)
+        fn(mps, mpo, p, 1, stream=stream)
+        n0, e0 = tdvp.norm(mps), tdvp.energy(mps, mpo)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fn(mps, mpo, p, 1, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        out[name] = {"ms_per_step": ms, "time_steps_per_s": 1e3 / ms, "norm_change": tdvp.norm(mps) - n0,
+                     "energy_change": tdvp.energy(mps, mpo) - e0, "bond_dims_max": int(max(mps.bond_dims()))}
+    print(json.dumps({"tdvp1_case": w.name, "chi": chi, "dtype": "f64", **out,
+                      "speedup_one_site": out["two_site"]["ms_per_step"] / out["one_site"]["ms_per_step"]}),
+          flush=True)
 
 
 def workload(args):
@@ -622,6 +661,9 @@ def main():
         return
     if args.xxx_case:
         xxx_case(args)
+        return
+    if args.tdvp1_case:
+        tdvp1_case(args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
