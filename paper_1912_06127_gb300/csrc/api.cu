@@ -6,6 +6,12 @@
 // SVD re-split (Fig. 5) and the environment updates (Eq. 19) -- as one set of
 // batched launches, followed by all one-site backward updates of the stage
 // (Eq. 20). One synchronisation per stage reads the new bond dimensions.
+//
+// Also here: two-site DMRG (dmrg_impl), measurements by transfer matrices,
+// the forward-mode derivative of the sweep with respect to h and J
+// (step_tangent_impl, measure_tangent_impl; kernels in tangent.cu), one-site
+// operators and mixed expectations for dynamical correlations, and the one-site
+// TDVP step with the hybrid two-site -> one-site scheme (step1_impl).
 #include <cmath>
 #include <cstring>
 #include <functional>
