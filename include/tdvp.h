@@ -120,6 +120,19 @@ typedef struct {
 
 /* ---- library / device ---- */
 
+/* Device memory through the caller's allocator: every buffer the library
+ * allocates afterwards (states, environments, MPO blocks, workspaces) comes from
+ * alloc(bytes, ctx) -- which returns device memory or NULL (then TDVP_ENOMEM) --
+ * and goes back through the free function registered with it, free(ptr, ctx),
+ * after the library has synchronised the device (a caching allocator may reuse
+ * the block at once). alloc = free = NULL restores cudaMalloc / cudaFree; blocks
+ * already handed out keep their own free function. The Python binding offers
+ * torch's caching allocator (use_torch_allocator). TDVP_EINVAL if exactly one of
+ * alloc and free is NULL. */
+typedef void* (*tdvp_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*tdvp_free_fn)(void* ptr, void* ctx);
+int tdvp_set_allocator(tdvp_alloc_fn alloc, tdvp_free_fn free_fn, void* ctx);
+
 /* Thread-local message of the last failure ("" if none). */
 const char* tdvp_last_error(void);
 /* Library version string. */

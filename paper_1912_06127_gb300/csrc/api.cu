@@ -776,6 +776,13 @@ void site_matrix(tdvp_mps_s* S, int j, double2* dst, cudaStream_t s);
 extern "C" {
 
 const char* tdvp_last_error(void) { return g_last_error.c_str(); }
+
+int tdvp_set_allocator(tdvp_alloc_fn alloc, tdvp_free_fn free_fn, void* ctx) {
+  return ok_or_code([&] {
+    if ((alloc == nullptr) != (free_fn == nullptr)) fail(TDVP_EINVAL, "alloc and free must both be set or both NULL");
+    set_allocator(alloc, free_fn, ctx);
+  });
+}
 const char* tdvp_version(void) { return "libtdvp 0.1 (sm_103a)"; }
 
 int tdvp_device_ok(void) {

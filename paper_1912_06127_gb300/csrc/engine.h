@@ -14,6 +14,7 @@ namespace tdvp {
 template <class T>
 T* dalloc(size_t n);
 void dfree(void* p);
+void set_allocator(tdvp_alloc_fn a, tdvp_free_fn f, void* ctx);
 
 // Sparse MPO operator on the device (CSR over the output bond index).
 struct DeviceWOp {

@@ -9,14 +9,52 @@
 // with D = d^2 and W = W_j W_{j+1} (merged on the host) for two sites, D = d for one.
 #include <algorithm>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "engine.h"
 
 namespace tdvp {
+
+// Optional caller-supplied allocator (tdvp_set_allocator). Blocks it hands out
+// are remembered with the function that returns them, so changing or removing
+// the allocator later still frees each block through its own allocator.
+namespace {
+std::mutex g_alloc_mutex;
+tdvp_alloc_fn g_user_alloc = nullptr;
+tdvp_free_fn g_user_free = nullptr;
+void* g_user_ctx = nullptr;
+struct UserBlock {
+  tdvp_free_fn free;
+  void* ctx;
+};
+std::unordered_map<void*, UserBlock> g_user_blocks;
+}  // namespace
+
+void set_allocator(tdvp_alloc_fn a, tdvp_free_fn f, void* ctx) {
+  std::lock_guard<std::mutex> g(g_alloc_mutex);
+  g_user_alloc = a;
+  g_user_free = f;
+  g_user_ctx = ctx;
+}
 
 template <class T>
 T* dalloc(size_t n) {
   void* p = nullptr;
   if (n == 0) n = 1;
+  {
+    std::unique_lock<std::mutex> g(g_alloc_mutex);
+    if (g_user_alloc) {
+      const tdvp_alloc_fn a = g_user_alloc;
+      const UserBlock blk{g_user_free, g_user_ctx};
+      g.unlock();
+      p = a(n * sizeof(T), blk.ctx);
+      if (!p) fail(TDVP_ENOMEM, "the caller's allocator returned NULL for " + std::to_string(n * sizeof(T)) + " bytes");
+      g.lock();
+      g_user_blocks[p] = blk;
+      return (T*)p;
+    }
+  }
   cudaError_t e = cudaMalloc(&p, n * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -31,7 +69,24 @@ template float2* dalloc<float2>(size_t);
 template int* dalloc<int>(size_t);
 template LzState* dalloc<LzState>(size_t);
 void dfree(void* p) {
-  if (p) cudaFree(p);
+  if (!p) return;
+  UserBlock blk{nullptr, nullptr};
+  {
+    std::lock_guard<std::mutex> g(g_alloc_mutex);
+    auto it = g_user_blocks.find(p);
+    if (it != g_user_blocks.end()) {
+      blk = it->second;
+      g_user_blocks.erase(it);
+    }
+  }
+  if (blk.free) {
+    // the library's kernels may still use the block on any stream; a caching
+    // allocator may hand it out again at once
+    cudaDeviceSynchronize();
+    blk.free(p, blk.ctx);
+    return;
+  }
+  cudaFree(p);
 }
 
 int64_t pad4(int64_t x) { return (x + 3) & ~(int64_t)3; }

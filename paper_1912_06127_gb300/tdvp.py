@@ -65,6 +65,9 @@ class DmrgStats(ctypes.Structure):
 
 _lib = None
 _P = ctypes.c_void_p
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_keep = None  # the registered callbacks must outlive their use
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 
@@ -81,6 +84,7 @@ def lib():
         "tdvp_last_error": ([], ctypes.c_char_p),
         "tdvp_version": ([], ctypes.c_char_p),
         "tdvp_device_ok": ([], ctypes.c_int),
+        "tdvp_set_allocator": ([_ALLOC, _FREE, _P], ctypes.c_int),
         "tdvp_fit_power_law": ([ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D], ctypes.c_int),
         "tdvp_build_mpo": ([ctypes.POINTER(Model), ctypes.POINTER(_P)], ctypes.c_int),
         "tdvp_fit_power_law_lm": ([ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D],
@@ -142,6 +146,29 @@ def lib():
         f.restype = res
     _lib = L
     return L
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route the library's device memory through torch's caching allocator
+    (enable=False: back to cudaMalloc / cudaFree for new blocks)."""
+    global _allocator_keep
+    if not enable:
+        _check(lib().tdvp_set_allocator(_ALLOC(), _FREE(), None))
+        return
+    import torch
+
+    def alloc(n, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(n)))
+        except Exception:
+            return None
+
+    def free(p, ctx):
+        torch.cuda.caching_allocator_delete(p)
+
+    cbs = (_ALLOC(alloc), _FREE(free))
+    _check(lib().tdvp_set_allocator(cbs[0], cbs[1], None))
+    _allocator_keep = (cbs, _allocator_keep)  # earlier callbacks may still own blocks
 
 
 def last_error() -> str:
