@@ -161,6 +161,11 @@ int tdvp_fit_power_law(double alpha, int n_exp, int r_max, double* x_out, double
 int tdvp_fit_power_law_lm(double alpha, int n_exp, int r_max, int relative, double* x_out, double* lam_out,
                           double* rms_out);
 int tdvp_build_mpo(const tdvp_model* model, tdvp_mpo* out);
+/* Host only: the couplings V(r) = sum_k x_k lam_k^r, r = 1..r_max, that an MPO
+ * with these exponentials realises (Sec. II C): 2*r_max doubles (complex). */
+int tdvp_couplings(int n_exp, const double* x, const double* lam, int r_max, double* V_out);
+/* The same for the exponentials held by `mpo`. */
+int tdvp_mpo_couplings(tdvp_mpo mpo, int r_max, double* V_out);
 /* MPO bond dimension m and physical dimension d. */
 int tdvp_mpo_dims(tdvp_mpo mpo, int* m, int* d);
 /* Copy the bulk tensor W (2*m*m*d*d doubles) and the couplings x, lam

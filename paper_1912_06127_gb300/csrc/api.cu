@@ -807,6 +807,30 @@ int tdvp_fit_power_law(double alpha, int n_exp, int r_max, double* x_out, double
   });
 }
 
+int tdvp_couplings(int n_exp, const double* x, const double* lam, int r_max, double* V_out) {
+  return ok_or_code([&] {
+    if (n_exp < 1 || r_max < 1 || !x || !lam || !V_out) fail(TDVP_EINVAL, "need n_exp >= 1, r_max >= 1, arrays");
+    const double2* xx = reinterpret_cast<const double2*>(x);
+    const double2* ll = reinterpret_cast<const double2*>(lam);
+    for (int r = 1; r <= r_max; ++r) {
+      double2 v = make_double2(0, 0);
+      for (int k = 0; k < n_exp; ++k) {
+        double2 p = make_double2(1, 0);  // lam_k^r by repeated multiplication
+        for (int e = 0; e < r; ++e) p = zmul(p, ll[k]);
+        v = zadd(v, zmul(xx[k], p));
+      }
+      V_out[2 * (r - 1)] = v.x;
+      V_out[2 * (r - 1) + 1] = v.y;
+    }
+  });
+}
+
+int tdvp_mpo_couplings(tdvp_mpo mpo, int r_max, double* V_out) {
+  if (!mpo) return ok_or_code([] { fail(TDVP_EINVAL, "NULL mpo"); });
+  return tdvp_couplings(mpo->n_exp, reinterpret_cast<const double*>(mpo->x.data()),
+                        reinterpret_cast<const double*>(mpo->lam.data()), r_max, V_out);
+}
+
 int tdvp_fit_power_law_lm(double alpha, int n_exp, int r_max, int relative, double* x_out, double* lam_out,
                           double* rms_out) {
   return ok_or_code([&] {

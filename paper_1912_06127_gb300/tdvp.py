@@ -87,6 +87,8 @@ def lib():
         "tdvp_set_allocator": ([_ALLOC, _FREE, _P], ctypes.c_int),
         "tdvp_fit_power_law": ([ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D], ctypes.c_int),
         "tdvp_build_mpo": ([ctypes.POINTER(Model), ctypes.POINTER(_P)], ctypes.c_int),
+        "tdvp_couplings": ([ctypes.c_int, _D, _D, ctypes.c_int, _D], ctypes.c_int),
+        "tdvp_mpo_couplings": ([_P, ctypes.c_int, _D], ctypes.c_int),
         "tdvp_fit_power_law_lm": ([ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D],
                                   ctypes.c_int),
         "tdvp_mpo_dims": ([_P, _I, _I], ctypes.c_int),
@@ -232,6 +234,16 @@ def fit_power_law_lm(alpha: float, n_exp: int, r_max: int, relative: bool = True
     return x, lam, rms.value
 
 
+def couplings(x: np.ndarray, lam: np.ndarray, r_max: int) -> np.ndarray:
+    """V(r) = sum_k x_k lam_k^r for r = 1..r_max (complex)."""
+    xa = np.ascontiguousarray(x, dtype=np.complex128)
+    la = np.ascontiguousarray(lam, dtype=np.complex128)
+    out = _cplx_out(r_max)
+    _check(lib().tdvp_couplings(len(xa), _dptr(xa.view(np.float64)), _dptr(la.view(np.float64)), r_max,
+                                _dptr(out.view(np.float64))))
+    return out
+
+
 class Mpo:
     def __init__(self, handle):
         self.handle = handle
@@ -245,6 +257,11 @@ class Mpo:
         m, d = ctypes.c_int(), ctypes.c_int()
         _check(lib().tdvp_mpo_dims(self.handle, ctypes.byref(m), ctypes.byref(d)))
         return m.value, d.value
+
+    def couplings(self, r_max: int) -> np.ndarray:
+        out = _cplx_out(r_max)
+        _check(lib().tdvp_mpo_couplings(self.handle, r_max, _dptr(out.view(np.float64))))
+        return out
 
     def tensor(self, n_exp: int):
         m, d = self.dims()

@@ -168,3 +168,11 @@ def test_new_entry_points_reject_bad_arguments(tdvp):
     assert L.tdvp_apply_site_op(None, 0, None) == -1
     assert L.tdvp_expect_mixed(None, None, 0, None) == -1
     assert "NULL" in tdvp.last_error() or tdvp.last_error()
+
+
+def test_couplings_match_oracle(tdvp):
+    x, lam = models.fit_power_law(2.0, 9, 200)
+    V = tdvp.couplings(x, lam, 200)
+    assert np.abs(V - models.couplings(x, lam, 200)).max() < 1e-13
+    # and the power law they approximate (the fit's own error, Supplemental Material)
+    assert np.abs(V.real - np.arange(1, 201) ** -2.0).max() < 1.5e-7
