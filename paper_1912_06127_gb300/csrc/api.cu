@@ -17,6 +17,8 @@
 #include <functional>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "engine.h"
 
 using namespace tdvp;
@@ -525,8 +527,11 @@ void step_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_st
   build_half(S->N, seg, 2, p->merge_turning, halves[1]);
   const int64_t l0 = g_launches;
   if (S->env_id != M->id) build_all_envs(S, M, s);
+  // NVTX ranges (no cost without a tool attached): step > half > stage > fwd2 / back1
   for (int step = 0; step < n_steps; ++step) {
+    nvtxRangePushA("tdvp_step");
     for (int h = 0; h < 2; ++h) {
+      nvtxRangePushA(h == 0 ? "half_1" : "half_2");
       const auto& ops = halves[h];
       size_t i = 0;
       while (i < ops.size()) {
@@ -537,12 +542,24 @@ void step_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_st
           else b.push_back(StageOp{ops[i].j, ops[i].tfac, 0});
           ++i;
         }
-        if (!f.empty()) run_fwd2(S, M, f, p, st, s);
-        if (!b.empty()) run_back1(S, M, b, p, st, s);
+        nvtxRangePushA("stage");
+        if (!f.empty()) {
+          nvtxRangePushA("fwd2");
+          run_fwd2(S, M, f, p, st, s);
+          nvtxRangePop();
+        }
+        if (!b.empty()) {
+          nvtxRangePushA("back1");
+          run_back1(S, M, b, p, st, s);
+          nvtxRangePop();
+        }
+        nvtxRangePop();
         if (st) st->n_stages += 1;
       }
+      nvtxRangePop();
     }
     read_stage_results(S, 0, s);
+    nvtxRangePop();
   }
   if (st) {
     st->kernel_launches += g_launches - l0;
