@@ -148,7 +148,6 @@ int tdvp_device_ok(void);
  * TDVP_EINVAL for n_exp < 1, n_exp > 64, r_max < 2 or alpha <= 0. */
 int tdvp_fit_power_law(double alpha, int n_exp, int r_max, double* x_out, double* lam_out);
 
-/* Build the MPO of a model on the current device. Host arrays are copied. */
 /* Host only. The Levenberg-Marquardt alternative to tdvp_fit_power_law that
  * the Supplemental Material compares for 1/r^2: real x_k, lam_k minimising the
  * sum over r = 1..r_max of (w_r e_r)^2, e_r = sum_k x_k lam_k^r - r^-alpha,
@@ -160,6 +159,7 @@ int tdvp_fit_power_law(double alpha, int n_exp, int r_max, double* x_out, double
  * pass them to tdvp_build_mpo through tdvp_model.x / .lam. */
 int tdvp_fit_power_law_lm(double alpha, int n_exp, int r_max, int relative, double* x_out, double* lam_out,
                           double* rms_out);
+/* Build the MPO of a model on the current device. Host arrays are copied. */
 int tdvp_build_mpo(const tdvp_model* model, tdvp_mpo* out);
 /* Host only: the couplings V(r) = sum_k x_k lam_k^r, r = 1..r_max, that an MPO
  * with these exponentials realises (Sec. II C): 2*r_max doubles (complex). */
@@ -171,6 +171,7 @@ int tdvp_mpo_dims(tdvp_mpo mpo, int* m, int* d);
 /* Copy the bulk tensor W (2*m*m*d*d doubles) and the couplings x, lam
  * (2*n_exp doubles each; any pointer may be NULL). Host only. */
 int tdvp_mpo_tensor(tdvp_mpo mpo, double* W_out, double* x_out, double* lam_out);
+/* Release an MPO handle (NULL is ignored). */
 void tdvp_free_mpo(tdvp_mpo mpo);
 
 /* ---- state (Sec. II A/B: inverse canonical gauge, Eq. 9) ---- */
@@ -203,6 +204,7 @@ int tdvp_mps_get_site(tdvp_mps mps, int j, double* out);
 int tdvp_mps_get_bond(tdvp_mps mps, int j, double* out);
 /* Site count N and physical dimension d. */
 int tdvp_mps_size(tdvp_mps mps, int* N, int* d);
+/* Release a state handle and its device memory (NULL is ignored). */
 void tdvp_free_mps(tdvp_mps mps);
 
 /* ---- time evolution (Sec. III) ---- */
@@ -299,6 +301,7 @@ int tdvp_build_mpo_derivative(tdvp_mpo mpo, int param, tdvp_mpo* out);
  * does not depend on the parameters). The tangent follows the bond dimensions
  * of `mps`; it stays valid only while `mps` is advanced by tdvp_step_tangent. */
 int tdvp_tangent_create(tdvp_mps mps, int n_dir, tdvp_tangent* out);
+/* Release a tangent handle (NULL is ignored). */
 void tdvp_free_tangent(tdvp_tangent tan);
 /* n_steps time steps of `mps` exactly as tdvp_step (FP64 only), advancing `tan`
  * along dmpo[0..n_dir) (derivative MPOs of `mpo`). n_quad in [1, 8] and
