@@ -152,7 +152,9 @@ def lib():
 
 def use_torch_allocator(enable: bool = True) -> None:
     """Route the library's device memory through torch's caching allocator
-    (enable=False: back to cudaMalloc / cudaFree for new blocks)."""
+    (enable=False: back to cudaMalloc / cudaFree for new blocks). Blocks taken
+    from torch go back to torch when their handle is released, so release the
+    library's handles while torch is still alive (not at interpreter exit)."""
     global _allocator_keep
     if not enable:
         _check(lib().tdvp_set_allocator(_ALLOC(), _FREE(), None))
