@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--precision", default="tf32x3", choices=sorted(PREC))
     ap.add_argument("--chi", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--fp64-steps", type=int, default=1,
-                    help="timed steps of the plain FP64 GPU path (after one warm-up step); 0 skips it")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="steps of the plain FP64 GPU path, each timed, compared step by step with the "
+                         "mixed path from the same state; 0 skips it")
     ap.add_argument("--svd-case", type=int, default=0,
                     help="profiling case: two truncated splits of one N x N two-site state "
                          "(half the spectrum kept), no benchmark line")
@@ -387,12 +388,17 @@ def fp64_peak_tflops():
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
-# DRAM bytes (read + write) per local problem of the Jacobi kernels, from one ncu
-# capture of a 512 x 512 split (profiles/svd_block_sweeps_split512.md); a launch
-# of the time step carries several problems, and its traffic scales with them
-# (each problem's vectors and rotation are read once and written once; the
-# sweeps run in L2). None once a kernel changes after the capture.
-TRAFFIC_PER_PROBLEM = {"svd_jacobi_fp32": 4.805888e6 + 4.152320e6, "svd_jacobi_dd": 8.535808e6 + 0.729088e6}
+# DRAM bytes (read + write) per local problem of a kernel kind, from one ncu
+# capture of the kernel on a single 512 x 512 split (`--svd-case 512`); a
+# launch of the time step carries several problems and its traffic scales with
+# them. Emptied whenever a listed kernel changes after its capture, so that no
+# stale figure is reported.
+TRAFFIC_PER_PROBLEM = {}
+
+
+def sm_count():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def roofline(prof, steps, clk=None, kernel=None, problems=None):
@@ -416,12 +422,13 @@ def roofline(prof, steps, clk=None, kernel=None, problems=None):
              "peak_source": "%s bf16 x 1.1/2.25 (TF32 nominal ratio)%s" % (src, " / 3 (3xTF32)" if passes == 3 else ""),
              "tensor_pipe_frac": ach * passes / tf32}
     elif dom == "svd_jacobi_fp32":
-        # FP32 ALU peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x clock
+        # FP32 ALU peak from unit counts and clocks: SMs x 128 FP32 lanes x 2 flops x clock
         mhz = (clk or {}).get("sm_mhz") or 2070.0
-        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        sms = sm_count()
+        peak = sms * 128 * 2 * mhz * 1e6 / 1e12
         ach = d["flops"] / d["launches"] / (ms_launch * 1e-3) / 1e12
         r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-             "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock)" % mhz}
+             "peak_source": "%d SMs (device query) x 128 FP32 lanes x 2 x %.0f MHz (median SM clock)" % (sms, mhz)}
     elif dom.startswith("zgemm") or dom.startswith("svd") or dom.startswith("theta"):
         peak = fp64_peak_tflops()
         ach = d["flops"] / d["launches"] / (ms_launch * 1e-3) / 1e12
@@ -487,12 +494,35 @@ def cpu_baseline_sample(chi, seconds_budget=30.0):
         cores = os.cpu_count()
     return {
         "value": 1.0 / t_step, "unit": UNIT, "cores": cores, "kind": "oracle",
-        "sample": ("numpy oracle at chi=%d: one two-site H_eff (%.2fs), one one-site H_eff (%.2fs), one "
-                   "512x512 SVD split (%.2fs), one environment update (%.2fs); scaled to one time step by "
-                   "%d two-site updates x %d Lanczos vectors + %d one-site updates x %d + %d environment "
-                   "updates with every bond at chi" % (chi, t_h2, t_h1, t_svd, t_env, n_f, k, n_b, k, n_env)),
+        "method": "per-operation extrapolation (not a timed step)",
+        "sample": ("per-operation extrapolation of the numpy oracle at chi=%d: one two-site H_eff (%.2fs), one "
+                   "one-site H_eff (%.2fs), one 512x512 SVD split (%.2fs), one environment update (%.2fs), "
+                   "timed; scaled to one time step by %d two-site updates x %d Lanczos vectors + %d one-site "
+                   "updates x %d + %d environment updates with every bond at chi"
+                   % (chi, t_h2, t_h1, t_svd, t_env, n_f, k, n_b, k, n_env)),
         "sample_seconds": t_h2 + t_h1 + t_svd + t_env,
     }
+
+
+def oracle_step_measured(chi=32):
+    """One whole time step of the oracle (as it stands) on the same chain,
+    schedule and Lanczos settings, from the seeded random MPS at a bond
+    dimension the host finishes in seconds, timed end to end (the initial
+    canonicalisation excluded)."""
+    from oracle import models
+    from oracle import mps as M
+    from oracle import tdvp as T
+    w = I.tfim_n101_quench()
+    mdl, prm = w.model, w.params
+    x, lam = models.fit_power_law(mdl.alpha, mdl.n_exp, mdl.N - 1)
+    W = models.build_mpo_site(mdl.kind, mdl.J, mdl.h, x, lam)
+    eng = T.Engine(M.canonicalize(I.random_mps_tensors(mdl.N, chi, seed=0), chi, 1e-14), W)
+    t0 = time.perf_counter()
+    eng.step(T.Params(dt=prm.dt, chi_max=chi, eps=prm.eps, krylov_max=prm.krylov_max, krylov_tol=prm.krylov_tol,
+                      seg_len=prm.seg_len), 1)
+    dt = time.perf_counter() - t0
+    return {"chi": chi, "s_per_step": dt, "value": 1.0 / dt, "unit": UNIT,
+            "sample": "one full oracle time step of %s at chi=%d (seeded random MPS), timed" % (w.name, chi)}
 
 
 # ---------------------------------------------------------------------------
@@ -502,11 +532,12 @@ def run_reference(args, world, rank):
     w = workload(args)
     for _ in range(args.warmup):
         pass  # the oracle has no state to warm; the warm-up steps are the first samples below
-    vals = []
+    vals, samples = [], []
     t_all = time.perf_counter()
     for _ in range(max(args.steps, 1)):
         cb = cpu_baseline_sample(args.chi)
         vals.append(1.0 / cb["value"])
+        samples.append(cb["sample_seconds"])
     wall = time.perf_counter() - t_all
     t_step = float(np.median(vals))
     line = {
@@ -516,9 +547,13 @@ def run_reference(args, world, rank):
         "config": {"workload": w.name, "N": w.model.N, "chi_max": args.chi, "m": w.model.m,
                    "segments": w.params.seg_len, "dt": w.params.dt, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": 1.0 / t_step, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                         "sample": cb["sample"]},
+                         "method": cb["method"], "sample": cb["sample"] + " (median over the steps)"},
         "e2e": {"value": 1.0 / t_step, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall,
+        # ms_per_step is extrapolated from timed operations, not a timed step:
+        # each "step" here is one bounded sample of the workload's operations
+        "extrapolated": True,
+        "sample_s_per_step": float(np.median(samples)),
     }
     print(json.dumps(line), flush=True)
 
@@ -561,16 +596,29 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     barrier(world)
     ms_max = allreduce_max(ms, world)
-    # end to end through the public API: step, then read the step's observable
-    # (<sigma^z_j> for every site) back to the host
+    # end to end through the public API with host buffers: the job's input (the
+    # seeded site tensors, in pinned host memory) is copied in and brought to
+    # the inverse canonical gauge by tdvp_init_mps_tensors, then every step is
+    # tdvp_step followed by reading that step's observable (<sigma^z_j> for
+    # every site) back to the host
+    pinned = []
+    for a in raw:
+        t = torch.empty(a.size * 2, dtype=torch.float64, pin_memory=True)
+        t.numpy()[:] = a.reshape(-1).view(np.float64)
+        pinned.append(t)
+    host_in = [t.numpy().view(np.complex128).reshape(a.shape) for t, a in zip(pinned, raw)]
+    h2d_bytes = sum(a.nbytes for a in raw)
+    del mps
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     n_e2e = max(1, args.e2e_steps)
+    t0 = time.perf_counter()
+    mps = tdvp.init_mps_tensors(host_in, args.chi, 1e-14)
     for _ in range(n_e2e):
         tdvp.step(mps, mpo, p, 1, stream=stream)
         sz = tdvp.measure(mps, tdvp.OBS_SZ)
     torch.cuda.synchronize()
     e2e_s = allreduce_max((time.perf_counter() - t0) / n_e2e, world)
+    assert sz.shape == (mdl.N,) and np.all(np.isfinite(sz))
     if rank != 0:
         return
     value = job_value(args.steps, ms_max, world)
@@ -591,8 +639,11 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs larger than L2: state + environments %.1f GB" % state_gb(mdl, args.chi),
                    "parallelism": "replicas" if world > 1 else "single GPU, segments batched"},
         "clocks": clk,
-        "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": int(8 * mdl.N + stages_per_step * (4 + 12 * 8) + 4)},
+        "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "steps": n_e2e,
+                "h2d_bytes_per_step": int(h2d_bytes / n_e2e),
+                "d2h_bytes_per_step": int(8 * mdl.N + stages_per_step * (4 + 12 * 8) + 4),
+                "what": ("tdvp_init_mps_tensors from pinned host tensors (once per job, its copy amortised "
+                         "over the steps) + per step tdvp_step and tdvp_measure(<sigma^z_j>) to host")},
         "gpu_launches": int(st.kernel_launches),
         "roofline": rl,
         "roofline_heff_gemm": rl_heff,
@@ -608,40 +659,64 @@ def run_ours(args, world, rank, local):
         line["fp64_path"] = ref
     if not args.no_cpu_baseline:
         cb = cpu_baseline_sample(args.chi)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "method", "sample")}
+        line["cpu_baseline"]["measured_step"] = oracle_step_measured()
     print(json.dumps(line), flush=True)
 
 
 def fp64_reference(args, tdvp, w, mpo, stream):
-    """The plain FP64 GPU path on the same workload: time-steps/s over
-    --fp64-steps steps after one warm-up step (CUDA events on the stream), and
-    the largest difference of <sigma^z_j> between one mixed-precision step and
-    one FP64 step taken from the same seeded state."""
+    """The plain FP64 GPU path against the mixed path on the same workload and
+    from the same seeded state, step by step, for 1 + --fp64-steps steps: every
+    step of each path timed with CUDA events on the stream, and after every
+    step the largest difference of <sigma^z_j> between the paths (the mixed
+    path is held to 1e-5) and both paths' energies (their drift from the
+    initial energy is set by the truncation). The FP64 rate excludes the first
+    step, which also builds the environments."""
     import torch
     mdl, prm = w.model, w.params
     raw = I.random_mps_tensors(mdl.N, args.chi, seed=0)
-    sz, out = {}, {}
+    n = args.fp64_steps + 1
+    runs = {}
     for prec in (PREC[args.precision], I.FP64):
         mps = tdvp.init_mps_tensors(raw, args.chi, 1e-14)
         p = tdvp.step_params(dt=prm.dt, chi_max=args.chi, w_max=prm.w_max, eps=prm.eps,
                              krylov_max=prm.krylov_max, krylov_tol=prm.krylov_tol, precision=prec,
                              seg_len=prm.seg_len, merge_turning=1)
-        tdvp.step(mps, mpo, p, 1, stream=stream)
-        sz[prec] = tdvp.measure(mps, tdvp.OBS_SZ)
-        if prec == I.FP64:
+        e_init = tdvp.energy(mps, mpo)
+        ms, sz, en, wt = [], [], [], []
+        for _ in range(n):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            tdvp.step(mps, mpo, p, args.fp64_steps, stream=stream)
+            st = tdvp.step(mps, mpo, p, 1, stream=stream)
             e1.record(stream)
             torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            out = {"value": args.fp64_steps / (ms * 1e-3), "unit": UNIT, "steps": args.fp64_steps, "warmup": 1,
-                   "ms_per_step": ms / args.fp64_steps, "dtype": "f64"}
+            ms.append(e0.elapsed_time(e1))
+            sz.append(tdvp.measure(mps, tdvp.OBS_SZ))
+            en.append(tdvp.energy(mps, mpo))
+            wt.append(st.w_total)
+        runs[prec] = {"ms": ms, "sz": np.array(sz), "en": np.array(en), "w": np.cumsum(wt), "e_init": e_init}
         del mps
-    out["sigma_z_max_abs_diff_1_step"] = float(np.abs(sz[PREC[args.precision]] - sz[I.FP64]).max())
-    return out
+    mx, d = runs[PREC[args.precision]], runs[I.FP64]
+    ms_t = d["ms"][1:]
+    diff = np.abs(mx["sz"] - d["sz"]).max(axis=1)
+    return {
+        "value": len(ms_t) / (sum(ms_t) * 1e-3), "unit": UNIT, "steps": len(ms_t), "warmup": 1,
+        "ms_per_step": float(np.mean(ms_t)), "dtype": "f64",
+        "series": {
+            "steps": n,
+            "sigma_z_max_abs_diff": [float(v) for v in diff],
+            "sigma_z_max_abs_diff_max": float(diff.max()),
+            "energy_initial": d["e_init"],
+            "energy_drift_mixed": [float(v - mx["e_init"]) for v in mx["en"]],
+            "energy_drift_fp64": [float(v - d["e_init"]) for v in d["en"]],
+            "energy_abs_diff": [float(v) for v in np.abs(mx["en"] - d["en"])],
+            "w_total_mixed": [float(v) for v in mx["w"]],
+            "w_total_fp64": [float(v) for v in d["w"]],
+            "ms_per_step_mixed": [float(v) for v in mx["ms"]],
+        },
+    }
 
 
 def state_gb(mdl, chi):

@@ -393,23 +393,42 @@ int tdvp_op_split_prec(int precision, int rows, int cols, const double* theta, i
                        double* w, void* stream);
 
 /* Same as tdvp_op_heff with precision TDVP_FP64, for callers that cannot
- * allocate device memory (a stream capture that forbids allocation, a host
- * application that owns every device allocation, a real-time loop). The
- * paper has no counterpart: this is a deployment variant of the H_eff
- * application of Fig. 4. It calls no cudaMalloc, cudaFree or allocating
- * library routine: its intermediates and the sparse MPO blocks live in one
- * fixed device array of TDVP_NOALLOC_SCRATCH_BYTES bytes inside the library,
- * present on every GPU that loads it until the process exits. Problems whose
- * scratch, 2 * chi_l * m * D * chi_r * 16 bytes (D = d^2 for nsite = 2, d for
- * nsite = 1) plus the MPO blocks, exceeds that size are rejected with
- * TDVP_EINVAL. The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) and should come before any stream capture. All calls
- * share the array: calls whose work overlaps on the GPU race on it and must be
- * serialised by the caller. W is a host pointer; L, R, x, y are device
- * pointers as in tdvp_op_heff. Synchronises `stream`. */
+ * allocate device memory: plug-ins whose host application owns every device
+ * allocation through its own pool, or real-time loops that must never enter
+ * an allocator. The paper has no counterpart: this is a deployment variant of
+ * the H_eff application of Fig. 4. It calls no cudaMalloc, cudaFree or
+ * allocating library routine: its intermediates and the sparse MPO blocks
+ * live in one fixed device array of TDVP_NOALLOC_SCRATCH_BYTES bytes inside
+ * the library, present on every GPU that loads it until the process exits.
+ * Problems whose scratch, 2 * chi_l * m * D * chi_r * 16 bytes (D = d^2 for
+ * nsite = 2, d for nsite = 1) plus the MPO blocks, exceeds that size, or with
+ * m > TDVP_NOALLOC_MAX_M, are rejected with TDVP_EINVAL before any work. The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress)
+ * and should come before any stream capture. All calls share the array:
+ * calls whose work overlaps on the GPU race on it and must be serialised by
+ * the caller. Every call builds the two-site operator on the host
+ * (O(m^3 d^4) operations) and copies it from host memory. W is a host
+ * pointer; L, R, x, y are device pointers as in tdvp_op_heff. Synchronises
+ * `stream` before returning. */
 #define TDVP_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+#define TDVP_NOALLOC_MAX_M 64
 int tdvp_op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,
                          const double* R, const double* x, double* y, void* stream);
+
+/* ---- failure detection ---- */
+
+/* Number of polls a grid-barrier wait of the SVD's cooperative Jacobi sweeps
+ * makes before it gives up (Sec. III D monitors the norm error of the run;
+ * the bounded waits are this library's own safeguard, with no counterpart in
+ * the paper). A wait that gives up sets the status word and an abort word
+ * that makes every other block of the launch return at its next barrier;
+ * the calling entry point then returns TDVP_ETIMEOUT. A state handle whose
+ * tdvp_step failed keeps its status (its tensors are no longer a valid
+ * step); other handles and later kernel-level calls (tdvp_op_*) start from a
+ * cleared status. spins < 0 restores the default (2^24 polls of
+ * ~64 ns, about a second). Process-wide; takes effect at the next SVD
+ * launch. Returns TDVP_OK. */
+int tdvp_set_wait_limit(long long spins);
 
 /* ---- profiling ---- */
 

@@ -327,11 +327,13 @@ void read_stage_results(tdvp_mps_s* S, int n, cudaStream_t s) {
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   const int st = S->h_pinned[1];
+  // a wait that gave up comes first: what the later kernels of the stage
+  // computed from the abandoned work may have set the numeric bits too
   if (st & 1) fail(TDVP_ETIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
+  if (st & 32) fail(TDVP_ETIMEOUT, "a bounded grid barrier gave up (SVD sweeps)");
   if (st & (2 | 8)) fail(TDVP_ENUMERIC, "NaN or zero norm in a local update");
   if (st & 4) fail(TDVP_ENUMERIC, "tridiagonal eigen-solver did not converge");
   if (st & 16) fail(TDVP_ENUMERIC, "Jacobi SVD did not converge");
-  if (st & 32) fail(TDVP_ETIMEOUT, "a bounded grid barrier gave up (SVD sweeps)");
   if (st & 64) fail(TDVP_ENUMERIC, "SVD tail rule violated: a kept singular value lies below the tail threshold");
 }
 
@@ -953,7 +955,12 @@ int tdvp_init_mps_tensors(int N, int d, const int* dims, const double* const* te
         raw[j] = dalloc<double2>(std::max<int64_t>(n, (int64_t)d * chi_cap * std::max(dims[j + 1], chi_cap)));
         CUDA_TRY(cudaMemcpy(raw[j], tensors[j], sizeof(double2) * n, cudaMemcpyHostToDevice));
       }
-      canonicalize_device(S, raw, std::vector<int>(dims, dims + N + 1), chi_cap, eps, s);
+      try {
+        canonicalize_device(S, raw, std::vector<int>(dims, dims + N + 1), chi_cap, eps, s);
+      } catch (...) {
+        for (auto p : raw) dfree(p);
+        throw;
+      }
       for (auto p : raw) dfree(p);
     } catch (...) {
       free_mps(S);
@@ -1216,10 +1223,10 @@ struct OpCtx {
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaMemcpy(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st & 1) fail(TDVP_ETIMEOUT, "a bounded device wait gave up (tensor-core pipeline)");
+    if (st & 32) fail(TDVP_ETIMEOUT, "a bounded grid barrier gave up (SVD sweeps)");
     if (st & (2 | 8)) fail(TDVP_ENUMERIC, "NaN or zero norm");
     if (st & 4) fail(TDVP_ENUMERIC, "tridiagonal eigen-solver did not converge");
     if (st & 16) fail(TDVP_ENUMERIC, "Jacobi SVD did not converge");
-    if (st & 32) fail(TDVP_ETIMEOUT, "a bounded grid barrier gave up (SVD sweeps)");
     if (st & 64) fail(TDVP_ENUMERIC, "SVD tail rule violated: a kept singular value lies below the tail threshold");
   }
 };
@@ -1565,6 +1572,11 @@ int tdvp_profile_read(int idx, char* name, int name_len, double* ms, int64_t* la
 
 int tdvp_profile_read_aux(int idx, double* aux) {
   return profile_read_impl(idx, nullptr, 0, nullptr, nullptr, nullptr, nullptr, aux);
+}
+
+int tdvp_set_wait_limit(long long spins) {
+  svd_set_spin_limit(spins);
+  return TDVP_OK;
 }
 
 int tdvp_op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,

@@ -1,14 +1,14 @@
 // H_eff . x without any device allocation, for callers that cannot allocate.
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a CUDA
-// stream is being captured into a graph with allocation forbidden, plug-ins
-// whose host application owns every device allocation through its own pool,
-// or real-time loops that must not enter the allocator. For them
-// tdvp_op_heff_noalloc runs the FP64 two- or one-site H_eff application of
-// tdvp_op_heff with its two intermediates (the L-contracted state and the
-// MPO-applied state) and the sparse MPO blocks placed in one file-scope
-// device array of TDVP_NOALLOC_SCRATCH_BYTES bytes. That array exists on every
-// GPU that loads the library and is held until the process exits.
+// Some callers cannot call cudaMalloc: plug-ins whose host application owns
+// every device allocation through its own pool and forbids others, or
+// real-time loops that must never enter an allocator (whose cost and locking
+// are unbounded). For them tdvp_op_heff_noalloc runs the FP64 two- or
+// one-site H_eff application of tdvp_op_heff with its two intermediates (the
+// L-contracted state and the MPO-applied state) and the sparse MPO blocks
+// placed in one file-scope device array of TDVP_NOALLOC_SCRATCH_BYTES bytes.
+// That array exists on every GPU that loads the library and is held until the
+// process exits.
 //
 // The host cannot use the array's name as a device address, so its address
 // is looked up with cudaGetSymbolAddress once per device, with that device
@@ -18,14 +18,20 @@
 // zero (every intermediate is fully overwritten before it is read), but two
 // calls whose work overlaps on the GPU (different streams, or different host
 // threads on the same device) race on it and must be serialised by the caller.
+//
+// Each call builds the sparse two-site operator W_j W_{j+1} on the host
+// (O(m^3 d^4) operations: ~1e5 for m = 10, d = 2) and copies it from host
+// memory, then synchronises the stream before returning.
 #include <mutex>
 
 #include "common.h"
 
 namespace tdvp {
 
-// 32 MiB: enough for chi_l * chi_r * m * d^2 up to ~1M complex elements per
-// intermediate (e.g. chi = 128, m = 16, two sites).
+// 32 MiB: two intermediates of chi_l * m * D * chi_r complex doubles each
+// (D = d^2 for two sites) plus the MPO blocks, so 2 * chi_l * m * D * chi_r * 16
+// bytes must stay below it: e.g. chi = 128 with m = 14 and two sites
+// (29.4 MB), or chi = 256 with m = 6 and one site (25.2 MB).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TDVP_NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -55,9 +61,24 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 void op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,
                      const double* R, const double* x, double* y, cudaStream_t s) {
-  if ((nsite != 1 && nsite != 2) || chi_l < 1 || chi_r < 1 || m < 1 || d < 2 || d > 4)
+  // the dimension bounds of tdvp_op_heff, plus a bound on the MPO bond
+  // dimension that keeps the host-side operator build small, all checked
+  // before anything is built
+  if ((nsite != 1 && nsite != 2) || chi_l < 1 || chi_r < 1 || m < 1 || d < 2 || d > 4 || chi_l > 4096 ||
+      chi_r > 4096)
     fail(TDVP_EINVAL, "invalid dimensions");
+  if (m > TDVP_NOALLOC_MAX_M)
+    fail(TDVP_EINVAL, "tdvp_op_heff_noalloc: m = " + std::to_string(m) + " above TDVP_NOALLOC_MAX_M = " +
+                          std::to_string(TDVP_NOALLOC_MAX_M));
   const int D = nsite == 2 ? d * d : d;
+  {
+    const size_t need = 2 * (size_t)chi_l * m * D * chi_r * sizeof(double2);
+    if (need > (size_t)TDVP_NOALLOC_SCRATCH_BYTES)
+      fail(TDVP_EINVAL, "tdvp_op_heff_noalloc: problem needs " + std::to_string(need) +
+                            " bytes of scratch for its intermediates, more than the fixed " +
+                            std::to_string((size_t)TDVP_NOALLOC_SCRATCH_BYTES) +
+                            " (use tdvp_op_heff for larger problems)");
+  }
   // sparse MPO operator (CSR over the right bond index), built on the host
   std::vector<double2> Wd((const double2*)W, (const double2*)W + (size_t)m * m * d * d);
   std::vector<double2> Wop;

@@ -29,6 +29,7 @@
 // whose discarded weight sum_{j >= chi_w} lambda_j^2 is <= w_max, capped at
 // chi_max and at the values above eps * lambda_1, at least 1. Then
 // Psi_L = A' Lambda', Psi_R = Lambda' B', V' = Lambda'^{-1} (Sec. II B).
+#include <atomic>
 #include "common.h"
 #include "svd.h"
 
@@ -359,7 +360,7 @@ __device__ inline void jacobi_pair(const SvdDesc& P, int r, int pair, int lane) 
 // barrier return at once) if the other blocks did not arrive in time.
 // sync[0] = arrivals, sync[1] = generation, sync[3] = abort (sync[2]: unconverged
 // problems, sync[4..5]: visit counters of the block sweeps).
-__device__ inline bool grid_barrier(unsigned* sync, unsigned nblocks, int* status) {
+__device__ inline bool grid_barrier(unsigned* sync, unsigned nblocks, int* status, long long spin_limit) {
   __shared__ int ok_sh;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -380,7 +381,7 @@ __device__ inline bool grid_barrier(unsigned* sync, unsigned nblocks, int* statu
           ok_sh = 0;
           break;
         }
-        if (++spins > (1ll << 24)) {
+        if (++spins > spin_limit) {
           ok_sh = 0;
           atomicOr(status, 32);
           atomicExch(sync + 3, 1u);
@@ -569,10 +570,10 @@ __global__ void __launch_bounds__(SVD_WARPS * 32) svd_sweeps(const __grid_consta
         if (*(volatile int*)P.conv) continue;
         jacobi_pair<T>(P, r, w - off[pid], lane);
       }
-      if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
+      if (!grid_barrier(B.sync, gridDim.x, B.status, B.spin_limit)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) sweep_end<T>(B, stop, work_flops, 1);
-    if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
+    if (!grid_barrier(B.sync, gridDim.x, B.status, B.spin_limit)) return;
     if (*unconv == 0) return;
   }
   if (fatal && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, 16);
@@ -1148,10 +1149,10 @@ __global__ void __launch_bounds__(32 * W, MINB) svd_block_sweeps(const __grid_co
         rr_pair(nbp, br, u - off[pid], bi, bj);
         block_visit<T, W>(P, bi, bj, br == 0, use_order != 0, acc_mode, (R)tol, xs, seq, nrm);
       }
-      if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
+      if (!grid_barrier(B.sync, gridDim.x, B.status, B.spin_limit)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) sweep_end<T>(B, stop, work_flops, acc_mode == 0);
-    if (!grid_barrier(B.sync, gridDim.x, B.status)) return;
+    if (!grid_barrier(B.sync, gridDim.x, B.status, B.spin_limit)) return;
     if (*unconv == 0) return;
   }
   if (fatal && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, 16);
@@ -1459,8 +1460,15 @@ static bool block_sweeps(SvdBatch& b, float stop, double tol, int fatal, int use
   return true;
 }
 
+namespace {
+std::atomic<long long> g_spin_limit{SVD_SPIN_LIMIT_DEFAULT};
+}
+
+void svd_set_spin_limit(long long spins) { g_spin_limit = spins < 0 ? SVD_SPIN_LIMIT_DEFAULT : spins; }
+
 void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s) {
   if (b.n <= 0) return;
+  b.spin_limit = g_spin_limit.load();
   int64_t max_elems = 1;
   int npad_max = 2, nvec_max = 1;
   for (int i = 0; i < b.n; ++i) {

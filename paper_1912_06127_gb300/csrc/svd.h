@@ -38,6 +38,7 @@ struct SvdBatch {
                          // FP64 sweeps applied to Acc through an FP32-accumulated block rotation
   int* status;           // bit 8: NaN / zero state, 16: no convergence, 32: barrier timeout, 64: tail rule
   unsigned* sync;        // 8 words of device scratch: grid barrier, sweep loop, visit counters
+  long long spin_limit;  // polls of a grid-barrier wait before it gives up (set by svd_split)
   SvdDesc d[MAXB];
 };
 
@@ -48,5 +49,11 @@ struct SvdBatch {
 // write Psi_L, V, Psi_R.
 // h_flag: pinned host int.
 void svd_split(SvdBatch& b, int* d_flag, int* h_flag, cudaStream_t s);
+
+// Polls a grid-barrier wait of the Jacobi sweeps makes before it gives up
+// (status bit 32); spins < 0 restores the default. Process-wide; read by
+// every later svd_split.
+constexpr long long SVD_SPIN_LIMIT_DEFAULT = 1ll << 24;
+void svd_set_spin_limit(long long spins);
 
 }  // namespace tdvp

@@ -129,6 +129,7 @@ def lib():
         "tdvp_profile": ([ctypes.c_int], ctypes.c_int),
         "tdvp_profile_read_aux": ([ctypes.c_int, _D], ctypes.c_int),
         "tdvp_op_heff_noalloc": ([ctypes.c_int] * 5 + [_D, _P, _P, _P, _P, _P], ctypes.c_int),
+        "tdvp_set_wait_limit": ([ctypes.c_longlong], ctypes.c_int),
         "tdvp_profile_read": ([ctypes.c_int, ctypes.c_char_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int64),
                                _D, _D], ctypes.c_int),
         "tdvp_build_mpo_derivative": ([_P, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
@@ -545,6 +546,12 @@ def tridiag_expm(alpha: np.ndarray, beta: np.ndarray, t: float) -> np.ndarray:
     out = _cplx_out(len(a))
     _check(lib().tdvp_tridiag_expm(len(a), _dptr(a), _dptr(b), t, _dptr(out.view(np.float64))))
     return out
+
+
+def set_wait_limit(spins: int) -> None:
+    """Polls a grid-barrier wait of the SVD sweeps makes before giving up
+    (TDVP_ETIMEOUT); spins < 0 restores the default."""
+    _check(lib().tdvp_set_wait_limit(int(spins)))
 
 
 # ---- profiling -----------------------------------------------------------------

@@ -35,5 +35,12 @@ def hermitian_env(shape, seed):
     return 0.5 * (a + a.conj().transpose(2, 1, 0))
 
 
-def rel_err(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+def max_err(a, b):
+    """Element-wise error of `a` against the reference `b`: max |a - b| over
+    all elements, relative to max |b|. Every element is checked at the scale
+    of the largest one, so a wrong or missing tile fails even where its
+    entries are small."""
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    assert a.shape == b.shape, (a.shape, b.shape)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))

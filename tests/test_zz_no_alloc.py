@@ -1,9 +1,9 @@
 """The allocation-free H_eff entry point agrees with the allocating one.
 
 tdvp_op_heff_noalloc serves callers that cannot allocate device memory (a
-stream capture that forbids allocation, a host application that owns all
-device memory, a real-time loop): it keeps its intermediates in a fixed
-scratch array inside the library. This test calls it through the C ABI twice
+host application that owns all device memory through its own pool, a
+real-time loop that must not enter an allocator): it keeps its intermediates
+in a fixed scratch array inside the library. This test calls it through the C ABI twice
 in a row -- a two-site problem, then a smaller one-site problem that finds
 the first call's data still in the array -- and compares each result with
 tdvp_op_heff (FP64) to the tolerance of the other FP64 parity tests. It also
@@ -17,7 +17,7 @@ import pytest
 import tdvp_inputs as I
 from oracle import models
 
-from gpu_util import dev, hermitian_env, host, lib, rel_err, torch_or_skip
+from gpu_util import dev, hermitian_env, host, lib, max_err, torch_or_skip
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +45,7 @@ def test_noalloc_matches_allocating_entry_point_twice():
         tdvp.op_heff_noalloc(nsite, chi_l, chi_r, m, d, W, Ld, Rd, xd, y_new)
         a, b = host(y_new), host(y_ref)
         assert np.all(np.isfinite(a))
-        assert rel_err(a, b) < 1e-12
+        assert max_err(a, b) < 1e-12
 
 
 def test_noalloc_rejects_problem_larger_than_scratch():
@@ -61,3 +61,17 @@ def test_noalloc_rejects_problem_larger_than_scratch():
     with pytest.raises(tdvp.TdvpError) as e:
         tdvp.op_heff_noalloc(2, chi, chi, m, d, W, L, R, xv, y)
     assert e.value.code == -1 and "scratch" in str(e.value)
+
+
+def test_noalloc_rejects_large_mpo_bond_dimension_before_building():
+    torch = torch_or_skip()
+    tdvp = lib()
+    m, d, chi = 65, 2, 2
+    W = np.zeros((m, m, d, d), complex)
+    L = torch.zeros(chi * m * chi, dtype=torch.complex128, device="cuda")
+    R = torch.zeros(chi * m * chi, dtype=torch.complex128, device="cuda")
+    xv = torch.zeros(chi * d * d * chi, dtype=torch.complex128, device="cuda")
+    y = torch.zeros(chi * d * d * chi, dtype=torch.complex128, device="cuda")
+    with pytest.raises(tdvp.TdvpError) as e:
+        tdvp.op_heff_noalloc(2, chi, chi, m, d, W, L, R, xv, y)
+    assert e.value.code == -1 and "TDVP_NOALLOC_MAX_M" in str(e.value)
