@@ -24,11 +24,13 @@ H0_eff(j) C = sum beta_{j+1}[a,w,a'] C[a',b'] gamma_j[b,w,b'] (Fig. 4 without W)
 """
 from __future__ import annotations
 
-from typing import Callable
+import dataclasses
+from typing import Callable, Dict, List, Tuple
 
 import numpy as np
 
-from .tdvp import Engine, Params, env_left, env_right, heff1_apply, lanczos_expm
+from .tdvp import (Engine, Params, env_left, env_right, heff1_apply, heff2_apply, lanczos_expm,
+                   segment_bounds, split_two_site, sweeps_right_first)
 
 
 def heff0_apply(L: np.ndarray, R: np.ndarray, C: np.ndarray) -> np.ndarray:
@@ -128,3 +130,143 @@ def step_hybrid(eng: Engine, p: Params, n_steps: int = 1) -> int:
         else:
             eng.step(p, 1)
     return n1
+
+
+# ---------------------------------------------------------------------------
+# Segmented (parallel) one-site TDVP, our reading of the paper's outlook on a
+# parallel 1TDVP. The chain is cut into the segments of the two-site scheme
+# (Sec. III B; directions, turning rules and waits as in oracle.tdvp.build_half)
+# and every segment runs the one-site sweep above over its own sites. The two
+# sites of a boundary are evolved together, as in the two-site scheme: the
+# left segment forms Theta = Psi_e V_e Psi_{e+1} (V = Lambda^-1, Sec. III B),
+# evolves it with H2_eff and splits it back at the bond's current dimension.
+# That pair step stands for the site terms of e and e+1 and the bond term
+# between them, so neither segment evolves its boundary site on its own: a
+# segment that leaves a boundary starts with the bond next to it. Boundaries
+# where the first half's sweeps converge get their pair step once by 2 tau at
+# the end of the first half (twice tau without merging); those where the
+# sweeps start get tau before the first half and tau after the second. With
+# one segment this is exactly step1; at full bond dimension it is exact, like
+# the serial sweep.
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Op1:
+    seg: int
+    kind: str        # "site" (forward, site j), "bond_r" / "bond_l" (bond_backward_right(j) /
+                     # bond_backward_left(j)), "pair" (boundary pair j, j+1)
+    j: int
+    tfac: int        # time in units of tau = dt/2
+    stage: int = -1
+    deps: Tuple[int, ...] = ()
+
+
+def build_half1(N: int, seg_len: List[int], half: int, merge: int) -> List[Op1]:
+    """Ops of one half of a segmented one-site time step, in stage order."""
+    segs = segment_bounds(N, seg_len)
+    p = len(segs)
+    turn = 2 if (half == 1 and merge) else 1
+    per_seg: List[List[Op1]] = [[] for _ in range(p)]
+    start_boundary: Dict[int, Op1] = {}
+    end_boundary: Dict[int, Op1] = {}
+    for k, (s, e) in enumerate(segs):
+        right = sweeps_right_first(k, p) if half == 1 else not sweeps_right_first(k, p)
+        q = per_seg[k]
+        if right:
+            if s == 0 and (half == 1 or not merge):
+                q.append(Op1(k, "site", 0, 1))
+            last_site = e if e == N - 1 else e - 1   # a boundary site is in the pair step
+            for j in range(s, e):
+                q.append(Op1(k, "bond_r", j, 1))
+                if j + 1 <= last_site:
+                    turning = (j + 1 == e) and (e == N - 1)
+                    q.append(Op1(k, "site", j + 1, turn if turning else 1))
+            if e < N - 1:
+                op = Op1(k, "pair", e, turn)
+                q.append(op)
+                end_boundary[k] = op
+        else:
+            if e == N - 1:
+                if half == 1 or not merge:
+                    q.append(Op1(k, "site", N - 1, 1))
+            elif half == 1 or not merge:
+                op = Op1(k, "pair", e, 1)
+                q.append(op)
+                start_boundary[k] = op
+            first_site = s if s == 0 else s + 1
+            for j in range(e, s, -1):
+                q.append(Op1(k, "bond_l", j, 1))
+                if j - 1 >= first_site:
+                    turning = (j - 1 == s) and (s == 0)
+                    q.append(Op1(k, "site", j - 1, turn if turning else 1))
+    changed = True
+    while changed:
+        changed = False
+        for k in range(p):
+            prev = -1
+            for i, op in enumerate(per_seg[k]):
+                st = prev + 1
+                if i == 0 and (k - 1) in start_boundary:
+                    st = max(st, start_boundary[k - 1].stage + 1)
+                if op is end_boundary.get(k):
+                    st = max(st, per_seg[k + 1][-1].stage + 1)
+                if st != op.stage:
+                    op.stage = st
+                    changed = True
+                prev = op.stage
+    ops = [op for k in range(p) for op in per_seg[k]]
+    ops.sort(key=lambda o: (o.stage, o.seg))
+    index = {id(o): i for i, o in enumerate(ops)}
+    for k in range(p):
+        for i, op in enumerate(per_seg[k]):
+            deps = []
+            if i > 0:
+                deps.append(index[id(per_seg[k][i - 1])])
+            if i == 0 and (k - 1) in start_boundary:
+                deps.append(index[id(start_boundary[k - 1])])
+            if op is end_boundary.get(k):
+                deps.append(index[id(per_seg[k + 1][-1])])
+            op.deps = tuple(deps)
+    return ops
+
+
+def boundary_pair(eng: Engine, e: int, t: float, p: Params) -> None:
+    """Sites e, e+1 evolved together by t (Eq. 18 with Theta = Psi_e V_e Psi_{e+1})
+    and split back at the bond's current dimension (the relative cutoff p.eps
+    still applies); beta_{e+1} and gamma_e rebuilt."""
+    mps, W = eng.mps, eng.W
+    chi = len(mps.V[e])
+    theta = np.einsum("asc,c,cub->asub", mps.Psi[e], mps.V[e], mps.Psi[e + 1])
+    L, R = eng.beta[e], eng.gamma[e + 1]
+    theta2, _ = lanczos_expm(lambda x: heff2_apply(L, W, W, R, x), theta, t, p.krylov_max, p.krylov_tol)
+    Psi_L, Vn, Psi_R, _, _ = split_two_site(theta2, chi, 0.0, p.eps)
+    mps.Psi[e], mps.V[e], mps.Psi[e + 1] = Psi_L, Vn, Psi_R
+    eng.beta[e + 1] = env_left(eng.beta[e], eng._A(e), W)
+    eng.gamma[e] = env_right(eng.gamma[e + 1], eng._B(e), W)
+
+
+def run_op1(eng: Engine, op: Op1, p: Params) -> None:
+    t = op.tfac * 0.5 * p.dt
+    if op.kind == "site":
+        site_forward(eng, op.j, t, p)
+    elif op.kind == "bond_r":
+        bond_backward_right(eng, op.j, t, p)
+    elif op.kind == "bond_l":
+        bond_backward_left(eng, op.j, t, p)
+    else:
+        boundary_pair(eng, op.j, t, p)
+
+
+def step1_segmented(eng: Engine, p: Params, n_steps: int = 1) -> None:
+    """n_steps symmetric one-site steps with the segments of p.seg_len (one
+    segment: the serial sweep of step1). At the start of a step gamma_0 and
+    beta_{N-1} are rebuilt from the current state, as step1 does for gamma_0."""
+    N = eng.mps.N
+    seg = p.seg_len if p.seg_len else [N]
+    halves = [build_half1(N, seg, 1, p.merge_turning), build_half1(N, seg, 2, p.merge_turning)]
+    for _ in range(n_steps):
+        eng.gamma[0] = env_right(eng.gamma[1], eng._B(0), eng.W)
+        eng.beta[N - 1] = env_left(eng.beta[N - 2], eng._A(N - 2), eng.W)
+        for half in halves:
+            for op in half:
+                run_op1(eng, op, p)

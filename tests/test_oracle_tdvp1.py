@@ -65,3 +65,72 @@ def test_hybrid_switches_when_bonds_saturate():
     assert T1.saturated(eng, 4)
     assert abs(M.norm2(eng.mps) - 1.0) < 1e-10
     assert abs(M.energy(eng.mps, W) - E0) < 1e-3 * abs(E0)
+
+
+# ---- segmented (parallel) one-site TDVP ----
+
+def _copy(mps):
+    import copy
+    return copy.deepcopy(mps)
+
+
+def test_segmented_one_site_with_one_segment_is_the_serial_sweep():
+    W, H, mps = setup(ISING, 8, 3.0, 4, 0.7, 6, 6, 11)
+    a, b = T.Engine(_copy(mps), W), T.Engine(_copy(mps), W)
+    p = T.Params(dt=0.05, chi_max=6, krylov_max=16, krylov_tol=0.0)
+    T1.step1(a, p, 3)
+    T1.step1_segmented(b, p, 3)
+    for x, y in zip(a.mps.Psi, b.mps.Psi):
+        assert np.array_equal(x, y)
+
+
+def test_segmented_schedule_covers_every_term_once_per_step():
+    """Per time step every site term acts forward for dt (one-site steps, or its
+    share of a boundary pair step) and every bond term backward for dt (a bond
+    step, or inside a boundary pair step)."""
+    for N, seg in ((10, [10]), (10, [5, 5]), (10, [3, 3, 4]), (11, [2, 3, 3, 3]), (12, [2, 2, 2, 2, 2, 2])):
+        for merge in (0, 1):
+            site = np.zeros(N)
+            bond = np.zeros(N - 1)
+            for half in (1, 2):
+                for op in T1.build_half1(N, seg, half, merge):
+                    if op.kind == "site":
+                        site[op.j] += op.tfac
+                    elif op.kind == "bond_r":
+                        bond[op.j] += op.tfac
+                    elif op.kind == "bond_l":
+                        bond[op.j - 1] += op.tfac
+                    else:
+                        site[op.j] += op.tfac
+                        site[op.j + 1] += op.tfac
+                        bond[op.j] += op.tfac
+            assert np.all(site == 2) and np.all(bond == 2), (N, seg, merge, site, bond)
+
+
+def test_segmented_one_site_is_exact_at_full_rank():
+    N = 8
+    W, H, mps = setup(ISING, N, 3.0, 4, 0.7, 16, 16, 3)
+    v0 = M.to_dense(mps)
+    ref = ed.expect_sz_dense(ed.ExactEvolution(H).evolve(v0, 0.3), N)
+    for seg in ([4, 4], [2, 3, 3], [2, 2, 2, 2]):
+        eng = T.Engine(_copy(mps), W)
+        T1.step1_segmented(eng, T.Params(dt=0.05, chi_max=16, krylov_max=24, krylov_tol=0.0, seg_len=seg), 6)
+        assert np.abs(M.expect_sz(eng.mps) - ref).max() < 1e-11, seg
+        assert abs(M.norm2(eng.mps) - 1.0) < 1e-12
+
+
+def test_segmented_one_site_below_full_rank():
+    """Bond dimensions are kept; the boundary pair steps cut back to them, so the
+    norm and energy drift by the discarded weight, which falls in proportion to
+    dt over a fixed time (a cut per boundary and step, each of order dt^2)."""
+    W, H, mps = setup(ISING, 10, 2.0, 4, 0.6, 4, 4, 7)
+    dims = mps.bond_dims()
+    E0 = M.energy(mps, W)
+    drift = []
+    for dt, n in ((0.05, 4), (0.025, 8)):
+        eng = T.Engine(_copy(mps), W)
+        T1.step1_segmented(eng, T.Params(dt=dt, chi_max=4, krylov_max=24, krylov_tol=0.0, seg_len=[3, 3, 4]), n)
+        assert eng.mps.bond_dims() == dims
+        assert M.norm2(eng.mps) <= 1.0 + 1e-12
+        drift.append(abs(M.energy(eng.mps, W) - E0))
+    assert drift[0] < 1e-2 and 0.4 * drift[0] < drift[1] < 0.6 * drift[0]
