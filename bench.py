@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--svd-case", type=int, default=0,
                     help="profiling case: two truncated splits of one N x N two-site state "
                          "(half the spectrum kept), no benchmark line")
+    ap.add_argument("--heff-case", type=int, default=0,
+                    help="profiling case: three two-site H_eff applications at chi_l = chi_r = N, m = 10, d = 2 "
+                         "(the benchmark's MPO) in --precision, through tdvp_op_heff; no benchmark line")
     ap.add_argument("--grad-case", action="store_true",
                     help="the differentiated 41-site Ising quench at chi 64: d<sigma^z_20(t)>/d(h, J) "
                          "by tdvp_step_tangent, timed, checked against central differences of tdvp_step")
@@ -63,8 +66,15 @@ def parse():
                     help="time steps of the 201-site 1/r^2 XXX chain (m = 32, chi 256, 16 uneven segments, "
                          "--precision) from a seeded random MPS at chi 256; no benchmark line")
     ap.add_argument("--xxx-steps", type=int, default=2)
+    ap.add_argument("--xxx-dmrg", action="store_true",
+                    help="with --xxx-case: the whole pipeline of the XXX quench -- two-site DMRG from the seeded "
+                         "random MPS at chi 16 up to chi 256, sigma^z at the central site, then --xxx-steps "
+                         "timed steps and the dynamical correlation at the last time")
     ap.add_argument("--tdvp1-case", action="store_true",
                     help="one-site vs two-site FP64 steps on the 41-site Ising chain at chi 64; no benchmark line")
+    ap.add_argument("--tune-case", action="store_true",
+                    help="mixed-precision steps of the 101-site chain at chi 64, 128 and 256 with fixed GEMM "
+                         "tiles and with the autotuner's; no benchmark line")
     ap.add_argument("--grad-init", default="random", choices=["random", "all_up"],
                     help="--grad-case start: seeded random MPS at chi 64 (every bond saturated, so every "
                          "step does the full chi = 64 work) or the all-up product state")
@@ -95,6 +105,40 @@ def svd_case(n, prec):
     print(json.dumps({"svd_case": n, "chi": chi, "w": w, "w_expected": w_ref}))
     if chi != n // 2 or abs(w - w_ref) > 1e-9 * float((s ** 2).sum()):
         raise SystemExit("svd case: unexpected truncation")
+
+
+def heff_case(chi, prec):
+    """Three H_eff . theta applications (Fig. 4a) at the benchmark's MPO (m = 10,
+    d = 2) with chi_l = chi_r = chi on seeded random environments and state,
+    through tdvp_op_heff: a small, self-contained case for kernel profiles of
+    the tensor-core GEMMs."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_06127_gb300 import tdvp
+    w = I.tfim_n101_quench()
+    mdl = w.model
+    mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
+    W = mpo.tensor(mdl.n_exp)[0]
+    m, d = W.shape[0], 2
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
+
+    L = dev(I.random_complex((chi, m, chi), 1))
+    R = dev(I.random_complex((chi, m, chi), 2))
+    th = dev(I.random_complex((chi, d, d, chi), 3))
+    y = torch.zeros(chi * d * d * chi, dtype=torch.complex128, device="cuda")
+    # the first call makes the autotuner's decisions; the last one (in the
+    # NVTX range "profiled") runs exactly what the time step runs
+    for it in range(3):
+        if it == 2:
+            torch.cuda.nvtx.range_push("profiled")
+        tdvp.op_heff(prec, 2, chi, chi, m, d, W, L, R, th, y)
+        torch.cuda.synchronize()
+        if it == 2:
+            torch.cuda.nvtx.range_pop()
+    print(json.dumps({"heff_case": chi, "precision": prec, "y_norm": float(torch.linalg.norm(y))}))
 
 
 def grad_case(args):
@@ -206,10 +250,31 @@ def xxx_case(args):
     mdl, prm = w.model, w.params
     prec = PREC[args.precision]
     mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
-    mps = tdvp.init_mps_tensors(I.random_mps_tensors(mdl.N, prm.chi_max, seed=0), prm.chi_max, 1e-14)
+    stream = torch.cuda.current_stream()
+    extra = {}
+    if args.xxx_dmrg:
+        # ground state: two-site DMRG (same H_eff kernels, Lanczos ground mode)
+        # from the seeded random MPS at chi 16, chi_max raised 32 -> 256
+        gs = tdvp.init_mps_tensors(I.random_mps_tensors(mdl.N, w.chi_init, seed=w.seed), prm.chi_max, 1e-14)
+        t0 = time.perf_counter()
+        sweeps = []
+        for chi, n in ((32, 2), (64, 2), (128, 2), (256, 3)):
+            ds = tdvp.dmrg(gs, mpo, tdvp.dmrg_params(chi, eps=prm.eps, krylov_max=8, krylov_tol=1e-8,
+                                                   precision=prec), n, stream=stream)
+            sweeps.append({"chi_max": chi, "sweeps": n, "energy": ds.energy, "w_total": ds.w_total})
+        torch.cuda.synchronize()
+        e0 = tdvp.energy(gs, mpo)
+        extra["dmrg"] = {"seconds": time.perf_counter() - t0, "schedule": sweeps, "E0": e0,
+                         "E0_per_site": e0 / mdl.N, "bond_dims_max": int(max(gs.bond_dims())),
+                         "context": "paper's E0/N = -0.410611165931 at chi 1024 with U(1) symmetry (Sec. IV C)"}
+        # sigma^z at the central site (0-based 100), evolved; C(r - k, t) = e^{-i E0 t} <psi0|sigma^z_r|psi(t)>
+        k = mdl.N // 2
+        mps = tdvp.mps_copy(gs)
+        tdvp.apply_site_op(mps, k, np.diag([1.0, -1.0]).astype(np.complex128))
+    else:
+        mps = tdvp.init_mps_tensors(I.random_mps_tensors(mdl.N, prm.chi_max, seed=0), prm.chi_max, 1e-14)
     p = tdvp.step_params(prm.dt, prm.chi_max, w_max=prm.w_max, eps=prm.eps, krylov_max=prm.krylov_max,
                          krylov_tol=prm.krylov_tol, precision=prec, seg_len=prm.seg_len)
-    stream = torch.cuda.current_stream()
     tdvp.step(mps, mpo, p, 1, stream=stream)
     clocks = ClockSampler(0)
     clocks.start()
@@ -225,8 +290,15 @@ def xxx_case(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     tot = sum(v["ms"] for v in prof.values())
+    if args.xxx_dmrg:
+        t_final = (1 + args.xxx_steps) * prm.dt
+        c = tdvp.expect_mixed(gs, mps, tdvp.OBS_SZ) * np.exp(-1j * extra["dmrg"]["E0"] * t_final)
+        extra["correlation"] = {"t": t_final, "site": k, "r": list(range(k - 5, k + 6)),
+                                "C_re": [float(v.real) for v in c[k - 5:k + 6]],
+                                "C_im": [float(v.imag) for v in c[k - 5:k + 6]],
+                                "sum_rule_sz_total": float(tdvp.measure(mps, tdvp.OBS_SZ).sum())}
     print(json.dumps({
-        "xxx_case": w.name, "time_steps_per_s": args.xxx_steps / (ms * 1e-3), "ms_per_step": ms / args.xxx_steps,
+        **extra, "xxx_case": w.name, "time_steps_per_s": args.xxx_steps / (ms * 1e-3), "ms_per_step": ms / args.xxx_steps,
         "steps": args.xxx_steps, "precision": args.precision, "m": mdl.m, "segments": prm.seg_len,
         "chi_max_seen": st.chi_max_seen, "gpu_launches": int(st.kernel_launches), "clocks": clk,
         "kernels": {k: {"ms": v["ms"], "share": v["ms"] / max(tot, 1e-9)}
@@ -238,8 +310,9 @@ def tdvp1_case(args):
     long-range Ising chain (alpha = 3, J = h = 1, 6 exponentials, dt = 0.02,
     chi = 64, Lanczos <= 8 vectors to 1e-10) from a seeded random MPS at chi = 64
     (every bond full, the regime where the hybrid scheme switches): one untimed
-    step of each, then one timed step of each (CUDA events); the one-site step's
-    norm and energy change."""
+    step of each, then one timed step of each (CUDA events), serial and with 8
+    segments (6, 5 x 7; all segments of a stage batched); each step's norm and
+    energy change."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -250,9 +323,12 @@ def tdvp1_case(args):
     mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
     raw = I.random_mps_tensors(mdl.N, chi, seed=4)
     p = tdvp.step_params(prm.dt, chi, eps=prm.eps, krylov_max=8, krylov_tol=1e-10)
+    seg = [6, 5, 5, 5, 5, 5, 5, 5]
+    pseg = tdvp.step_params(prm.dt, chi, eps=prm.eps, krylov_max=8, krylov_tol=1e-10, seg_len=seg)
     stream = torch.cuda.current_stream()
     out = {}
-    for name, fn in (("two_site", tdvp.step), ("one_site", tdvp.step1)):
+    for name, fn, p in (("two_site", tdvp.step, p), ("one_site", tdvp.step1, p),
+                        ("two_site_8_segments", tdvp.step, pseg), ("one_site_8_segments", tdvp.step1, pseg)):
         mps = tdvp.init_mps_tensors(raw, chi, 1e-14)
         fn(mps, mpo, p, 1, stream=stream)
         n0, e0 = tdvp.norm(mps), tdvp.energy(mps, mpo)
@@ -268,6 +344,46 @@ def tdvp1_case(args):
     print(json.dumps({"tdvp1_case": w.name, "chi": chi, "dtype": "f64", **out,
                       "speedup_one_site": out["two_site"]["ms_per_step"] / out["one_site"]["ms_per_step"]}),
           flush=True)
+
+
+def tune_case(args):
+    """The 101-site benchmark chain (3xTF32, 8 segments) from its seeded random
+    state at chi = 64, 128 and 256: one warm-up step (which also makes the
+    autotuner's decisions when it is on), then timed steps (CUDA events), with
+    fixed tiles and with tuned tiles; the tuned decisions are listed."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_06127_gb300 import tdvp
+    w = workload(args)
+    mdl, prm = w.model, w.params
+    mpo = tdvp.build_mpo(mdl.kind, mdl.N, mdl.alpha, mdl.J, mdl.h, mdl.n_exp)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for chi in (64, 128, 256):
+        raw = I.random_mps_tensors(mdl.N, chi, seed=0)
+        row = {}
+        for tuned in (False, True):
+            tdvp.set_autotune(tuned)
+            mps = tdvp.init_mps_tensors(raw, chi, 1e-14)
+            p = tdvp.step_params(dt=prm.dt, chi_max=chi, w_max=prm.w_max, eps=prm.eps,
+                                 krylov_max=prm.krylov_max, krylov_tol=prm.krylov_tol,
+                                 precision=PREC[args.precision], seg_len=prm.seg_len, merge_turning=1)
+            tdvp.step(mps, mpo, p, 1, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            tdvp.step(mps, mpo, p, args.steps, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row["tuned" if tuned else "fixed"] = e0.elapsed_time(e1) / args.steps
+            if tuned:
+                row["decisions"] = tdvp.autotune_report()
+            del mps
+        row["speedup"] = row["fixed"] / row["tuned"]
+        out[str(chi)] = row
+    tdvp.set_autotune(True)
+    print(json.dumps({"tune_case": w.name, "precision": args.precision, "ms_per_step": out}), flush=True)
 
 
 def workload(args):
@@ -652,6 +768,7 @@ def run_ours(args, world, rank, local):
                         "aux": v.get("aux", 0.0)}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
         "w_total": st.w_total, "chi_max_seen": st.chi_max_seen, "wall_s": wall,
+        "autotune": tdvp.autotune_report(),
     }
     if args.fp64_steps > 0 and args.precision != "fp64":
         ref = fp64_reference(args, tdvp, w, mpo, stream)
@@ -731,6 +848,9 @@ def main():
     if args.svd_case:
         svd_case(args.svd_case, PREC[args.precision])
         return
+    if args.heff_case:
+        heff_case(args.heff_case, PREC[args.precision])
+        return
     if args.grad_case:
         grad_case(args)
         return
@@ -739,6 +859,9 @@ def main():
         return
     if args.tdvp1_case:
         tdvp1_case(args)
+        return
+    if args.tune_case:
+        tune_case(args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

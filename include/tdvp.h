@@ -51,8 +51,30 @@ extern "C" {
 #define TDVP_FP64 0   /* complex FP64 throughout                                  */
 #define TDVP_TF32 1   /* tensor-core TF32 complex GEMMs, FP32 accumulate          */
 #define TDVP_TF32X3 2 /* 3xTF32 split-precision products, FP32 accumulate         */
-/* Lanczos orthogonalisation, the tridiagonal exponential, the SVD and
- * V = Lambda^-1 are FP64 in every mode. */
+/* Precision of every step, per mode:
+ *   - Lanczos recurrences and re-orthogonalisation, the tridiagonal
+ *     exponential and V = Lambda^-1: FP64 in every mode.
+ *   - H_eff applications: the mode's GEMMs (FP64 SIMT, or tcgen05 TF32 /
+ *     3xTF32 with FP32 accumulation). The tensor cores' FP32 accumulation
+ *     loses accuracy with every MMA step, so long sums are cut into chunks
+ *     summed in FP64; an H_eff application is then accurate to ~6e-6 to 1e-5
+ *     relative to its largest element in 3xTF32, ~4e-4 in TF32.
+ *   - Environment updates: FP64 (TDVP_FP64); in the mixed modes double-float
+ *     GEMMs on the FP32 pipe (~48 significant bits) unless
+ *     tdvp_set_env_tensor_cores moves them to the tensor cores.
+ *   - Theta = Psi V Psi and the measurements: FP64 (TDVP_FP64) or
+ *     double-float (mixed modes).
+ *   - Bond SVD: one-sided Jacobi. TDVP_FP64: an FP32 phase, then FP64 sweeps
+ *     to ~1e-14 relative orthogonality; isometries to ~1e-14. Mixed modes: the
+ *     FP32 phase, then double-float sweeps that stop at a relative
+ *     off-diagonal of 1e-4 (~1e-8 left), the unitary factor updated through
+ *     FP32-accumulated block rotations; isometries to ~1e-10 when the kept
+ *     singular values lie above ~1e-5 of the largest (the FP32 phase resolves
+ *     them), ~3e-7 when they reach down to its noise level (~1e-6).
+ * Measured on a 41-site Ising chain with every bond at chi = 64 (8 segments,
+ * dt = 0.01), <sigma^z_j> of TDVP_TF32X3 against TDVP_FP64 after 20 steps:
+ * 3.6e-7 (default); 1.1e-5 with tensor-core environments; ~2e-12 when only
+ * the SVD is the mixed one. */
 
 /* ---- observables for tdvp_measure ---- */
 #define TDVP_OBS_SZ 0
@@ -227,8 +249,18 @@ int tdvp_step(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_
  * H0_eff C = sum beta_{j+1}[a,w,a'] C[a',b'] gamma_j[b,w,b'], re-diagonalised (the
  * inverse canonical gauge restored) and moved into site j+1; the last site
  * forward by dt; then the mirror sweep, ending with site 0 forward by dt/2.
- * FP64 only, n_seg <= 1 (TDVP_EINVAL otherwise). Norm and energy are conserved
- * to the Lanczos accuracy. stats->n_back1 counts the site updates. */
+ * Norm and energy are conserved to the Lanczos accuracy.
+ * With n_seg > 1 the parallel form (the paper's outlook, read with the
+ * segments of Sec. III B): every segment runs this sweep over its own sites in
+ * the direction tdvp_step gives it, and the two sites of a boundary are
+ * evolved together as in tdvp_step (Theta = Psi_e V_e Psi_{e+1}, V = Lambda^-1)
+ * and split back at the bond's current dimension (cut only by eps), which
+ * stands for their site terms and the bond term between them; per stage the
+ * site steps and the boundary pairs of all segments run batched. Bond
+ * dimensions are kept; the boundary cuts change norm and energy by their
+ * discarded weight. Exact at full bond dimension. The schedule is
+ * tdvp_schedule1's. FP64 only. stats->n_back1 counts the site updates,
+ * stats->n_fwd2 the boundary pair updates. */
 int tdvp_step1(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps,
                tdvp_step_stats* stats, void* stream);
 /* The hybrid scheme: per step, a tdvp_step (two-site, any segmentation) while
@@ -415,6 +447,39 @@ int tdvp_op_split_prec(int precision, int rows, int cols, const double* theta, i
 int tdvp_op_heff_noalloc(int nsite, int chi_l, int chi_r, int m, int d, const double* W, const double* L,
                          const double* R, const double* x, double* y, void* stream);
 
+/* ---- environment precision of the mixed modes ---- */
+
+/* enable = 0 (the default): in TDVP_TF32 / TDVP_TF32X3 the environment
+ * updates (Eq. 19 and its mirror) run as double-float GEMMs on the FP32 pipe
+ * (~48 significant bits; the W stage in FP64) while H_eff runs on the tensor
+ * cores. An environment is reused by every later H_eff of the half sweep, so
+ * its error acts like a fixed perturbation of H and moves observables
+ * linearly in time; with tensor-core environments that drift was ~30x larger
+ * (41-site Ising chain, chi = 64: <sigma^z_j> 1.1e-5 from the FP64 path after
+ * 20 steps, against 3.6e-7). enable = 1: the environment updates use the
+ * mode's tensor-core products too (faster, less accurate). Process-wide; takes
+ * effect at the next environment update. Returns TDVP_OK. */
+int tdvp_set_env_tensor_cores(int enable);
+
+/* ---- GEMM tile autotuning ---- */
+
+/* enable != 0 (the default): the first GEMM launch of each family (tcgen05
+ * TF32 / 3xTF32 products, FP64 and double-float SIMT products) with a new
+ * shape -- its M, N, K (set by chi, the MPO bond dimension m and d) and batch
+ * size, bucketed to powers of two -- times every tile candidate on its own
+ * operands (tcgen05: N tile 256 or 128; SIMT: 64 x 64 or 32 x 32 outputs per
+ * CTA) with CUDA events on the launching stream and keeps the fastest for that
+ * shape. The candidates compute every output with the same operations, so
+ * tuning changes no result. A tuning launch synchronises its stream once.
+ * enable = 0: fixed tiles (tcgen05 N = 256; FP64 64 x 64; double-float 64 x 64
+ * when the batch has at least two tiles per SM, else 32 x 32). Either call
+ * forgets the decisions made so far. Process-wide. Returns TDVP_OK. */
+int tdvp_set_autotune(int enable);
+/* The decisions made so far as a JSON list (family, shape bucket, choice,
+ * microseconds per candidate), NUL-terminated in out (at most len bytes; out
+ * may be NULL to query). Returns the length of the full text, without NUL. */
+int tdvp_autotune_report(char* out, int len);
+
 /* ---- failure detection ---- */
 
 /* Number of polls a grid-barrier wait of the SVD's cooperative Jacobi sweeps
@@ -455,6 +520,15 @@ int tdvp_profile_read_aux(int idx, double* aux);
  * gamma_j), boundary flag, stage index. Returns the number of ops (out may be
  * NULL to query it) or a negative error code. */
 int tdvp_schedule(int N, int n_seg, const int* seg_len, int merge_turning, int half, int* out, int max_ops);
+
+/* The stage schedule of one half of a segmented one-site step (tdvp_step1
+ * with n_seg > 1), in tdvp_schedule's 7-int layout with kind 0 = one-site
+ * forward step on site j, 1 = bond j evolved backward with the centre moving
+ * right, 2 = bond j - 1 evolved backward with the centre moving left (site j
+ * split), 3 = boundary pair (j, j + 1) (boundary flag 1); the environment
+ * field is 0. Returns the number of ops (out may be NULL to query it) or a
+ * negative error code. */
+int tdvp_schedule1(int N, int n_seg, const int* seg_len, int merge_turning, int half, int* out, int max_ops);
 
 /* c = exp(-i t T) e_0 (2*k doubles) for the real symmetric tridiagonal T with
  * diagonal alpha[k] and off-diagonal beta[k-1] -- the small exponential of the

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtdvp.so")
 
-SOURCES = ["host_numerics", "schedule", "kernels_simt", "lanczos", "svd", "tc_gemm", "ops", "api", "profile", "noalloc", "tangent"]
+SOURCES = ["host_numerics", "schedule", "kernels_simt", "lanczos", "svd", "tc_gemm", "ops", "api", "profile", "noalloc", "tangent", "tune"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

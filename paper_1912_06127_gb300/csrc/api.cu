@@ -339,6 +339,7 @@ void read_stage_results(tdvp_mps_s* S, int n, cudaStream_t s) {
 
 struct StageOp {
   int j, tfac, env;
+  int chi_max = 0;  // > 0: this update's bond dimension cap instead of the step's chi_max
 };
 
 // Two-site updates of one stage. ground = false: Theta' = exp(-i H2_eff t) Theta
@@ -432,7 +433,7 @@ void run_fwd2(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<StageOp>& ops, con
     q.perm = sl[i]->perm;
     q.rotated = sl[i]->rot;
     q.conv = sl[i]->conv;
-    q.chi_max = std::min(p->chi_max, S->cap[j]);
+    q.chi_max = std::min(ops[i].chi_max > 0 ? ops[i].chi_max : p->chi_max, S->cap[j]);
     q.w_max = p->w_max;
     q.eps = p->eps;
     q.chi = S->d_chi + i;
@@ -1492,6 +1493,35 @@ int tdvp_op_split_prec(int precision, int rows, int cols, const double* theta, i
   });
 }
 
+int tdvp_schedule1(int N, int n_seg, const int* seg_len, int merge_turning, int half, int* out, int max_ops) {
+  int count = 0;
+  int rc = ok_or_code([&] {
+    if (half != 1 && half != 2) fail(TDVP_EINVAL, "half must be 1 or 2");
+    if (N < 2) fail(TDVP_EINVAL, "need N >= 2");
+    std::vector<int> seg;
+    if (n_seg <= 1 || !seg_len) seg = {N};
+    else seg.assign(seg_len, seg_len + n_seg);
+    std::vector<SchedOp> ops;
+    build_half1(N, seg, half, merge_turning, ops);
+    count = (int)ops.size();
+    if (out) {
+      if (max_ops < count) fail(TDVP_EINVAL, "output too small");
+      for (int i = 0; i < count; ++i) {
+        const SchedOp& o = ops[i];
+        int* r = out + 7 * i;
+        r[0] = o.seg;
+        r[1] = o.kind;
+        r[2] = o.j;
+        r[3] = o.tfac;
+        r[4] = o.env;
+        r[5] = o.boundary;
+        r[6] = o.stage;
+      }
+    }
+  });
+  return rc == TDVP_OK ? count : rc;
+}
+
 int tdvp_schedule(int N, int n_seg, const int* seg_len, int merge_turning, int half, int* out, int max_ops) {
   int count = 0;
   int rc = ok_or_code([&] {
@@ -1572,6 +1602,26 @@ int tdvp_profile_read(int idx, char* name, int name_len, double* ms, int64_t* la
 
 int tdvp_profile_read_aux(int idx, double* aux) {
   return profile_read_impl(idx, nullptr, 0, nullptr, nullptr, nullptr, nullptr, aux);
+}
+
+int tdvp_set_env_tensor_cores(int enable) {
+  set_env_on_tensor_cores(enable != 0);
+  return TDVP_OK;
+}
+
+int tdvp_set_autotune(int enable) {
+  tune_enable(enable != 0);
+  return TDVP_OK;
+}
+
+int tdvp_autotune_report(char* out, int len) {
+  const std::string r = tune_report();
+  if (out && len > 0) {
+    const size_t n = std::min<size_t>(r.size(), (size_t)len - 1);
+    std::memcpy(out, r.data(), n);
+    out[n] = 0;
+  }
+  return (int)r.size();
 }
 
 int tdvp_set_wait_limit(long long spins) {
@@ -2577,17 +2627,26 @@ void bond_backward_left(tdvp_mps_s* S, tdvp_mpo_s* M, int j, double tau, const t
   right_env(S, M, j - 1, s);
 }
 
+void step1_seg_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_steps, tdvp_step_stats* st,
+                    cudaStream_t s);
+
 void step1_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_steps, tdvp_step_stats* st,
                 cudaStream_t s) {
   check_params(S, M, p);
   if (p->precision != TDVP_FP64) fail(TDVP_EINVAL, "one-site sweeps are FP64 only");
-  if (p->n_seg > 1) fail(TDVP_EINVAL, "one-site sweeps are serial (n_seg <= 1)");
   ensure_small_buffers(S);
   ensure_w0(M);
   ensure_w1s(S);
   const int64_t l0 = g_launches;
   if (S->env_id != M->id) build_all_envs(S, M, s);
   const int N = S->N;
+  if (p->n_seg > 1 && p->seg_len) {
+    step1_seg_impl(S, M, p, n_steps, st, s);
+    S->beta32_ok.assign(N, 0);
+    S->gamma32_ok.assign(N, 0);
+    if (st) st->kernel_launches += g_launches - l0;
+    return;
+  }
   const double tau = 0.5 * p->dt;
   for (int step = 0; step < n_steps; ++step) {
     right_env(S, M, 0, s);  // gamma_0 of the current state (a two-site half leaves it behind)
@@ -2607,6 +2666,74 @@ void step1_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_s
   S->beta32_ok.assign(N, 0);
   S->gamma32_ok.assign(N, 0);
   if (st) st->kernel_launches += g_launches - l0;
+}
+
+// one-site forward steps of several sites at once (one batched Lanczos)
+void site_forward_batch(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<std::pair<int, double>>& js,
+                        const tdvp_step_params* p, tdvp_step_stats* st, cudaStream_t s) {
+  if (js.empty()) return;
+  std::vector<MvProb> P;
+  std::vector<const double2*> x;
+  std::vector<double2*> y;
+  std::vector<double> t;
+  for (size_t i = 0; i < js.size(); ++i) {
+    const int j = js[i].first, A = S->chiL(j), B = S->chiR(j);
+    Slot* sl = slot_for(S, (int)i, M->m, p->krylov_max);
+    P.push_back(make_mv(S, M, A, B, S->d, j, j, false, sl, TDVP_FP64));
+    x.push_back(S->Psi[j]);
+    y.push_back(S->Psi[j]);
+    t.push_back(js[i].second);
+    if (st) {
+      st->heff_flops += p->krylov_max * heff_flops(A, B, S->d, M->m, M->w1.nnz);
+      st->n_back1 += 1;
+    }
+  }
+  expm_batch(P, x, y, t, p->krylov_max, p->krylov_tol, Ctx{s, S->d_status, TDVP_FP64});
+}
+
+// Segmented one-site steps (build_half1): per stage the site steps run as one
+// batch, the boundary pairs as one batched two-site update at each bond's
+// current dimension, the bond steps one after another. Stages run in order;
+// the ops of a stage touch disjoint tensors, so their order does not matter.
+void step1_seg_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_steps, tdvp_step_stats* st,
+                    cudaStream_t s) {
+  const int N = S->N;
+  std::vector<int> seg(p->seg_len, p->seg_len + p->n_seg);
+  if ((int)seg.size() > MAXB) fail(TDVP_EINVAL, "too many segments");
+  std::vector<SchedOp> halves[2];
+  build_half1(N, seg, 1, p->merge_turning, halves[0]);
+  build_half1(N, seg, 2, p->merge_turning, halves[1]);
+  const double tau = 0.5 * p->dt;
+  tdvp_step_params pp = *p;  // boundary pairs: no weight cut beyond the relative cutoff
+  pp.w_max = 0.0;
+  for (int step = 0; step < n_steps; ++step) {
+    right_env(S, M, 0, s);      // gamma_0 and beta_{N-1} of the current state
+    left_env(S, M, N - 2, s);
+    for (int h = 0; h < 2; ++h) {
+      const auto& ops = halves[h];
+      size_t i = 0;
+      while (i < ops.size()) {
+        const int stage = ops[i].stage;
+        std::vector<std::pair<int, double>> sites;
+        std::vector<StageOp> pairs;
+        std::vector<const SchedOp*> bonds;
+        for (; i < ops.size() && ops[i].stage == stage; ++i) {
+          const SchedOp& o = ops[i];
+          if (o.kind == 0) sites.push_back({o.j, o.tfac * tau});
+          else if (o.kind == 3) pairs.push_back(StageOp{o.j, o.tfac, 3, S->dims[o.j]});
+          else bonds.push_back(&o);
+        }
+        site_forward_batch(S, M, sites, p, st, s);
+        for (const SchedOp* o : bonds) {
+          if (o->kind == 1) bond_backward_right(S, M, o->j, o->tfac * tau, p, s);
+          else bond_backward_left(S, M, o->j, o->tfac * tau, p, s);
+        }
+        if (!pairs.empty()) run_fwd2(S, M, pairs, &pp, st, s);
+        if (st) st->n_stages += 1;
+      }
+    }
+    read_stage_results(S, 0, s);
+  }
 }
 
 bool bonds_saturated(const tdvp_mps_s* S, int chi_max) {

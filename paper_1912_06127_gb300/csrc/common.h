@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,17 @@ void cuda_check(cudaError_t e, const char* what, const char* file, int line);
 
 // Global counter of kernels launched (for the statistics only).
 extern int64_t g_launches;
+
+// GEMM tile autotuner (tune.cu): run(c) launches candidate c of a family
+// (candidate 0 is the default); the first launch with a new shape key times
+// every candidate and keeps the fastest. may_repeat = false (the launch
+// accumulates into its output) always runs candidate 0 untuned.
+enum { TUNE_TC_TF32 = 0, TUNE_TC_TF32X3 = 1, TUNE_ZGEMM = 2, TUNE_ZGEMM_DD = 3 };
+int tune_pick(int family, int64_t M, int64_t N, int64_t K, int n, int n_cand, bool may_repeat,
+              const std::function<void(int)>& run, cudaStream_t s);
+void tune_enable(bool on);  // clears the decisions
+bool tune_enabled();
+std::string tune_report();  // the decisions as a JSON list
 
 // Optional per-kernel timing with CUDA events recorded on the launching
 // stream around each launch (enabled by tdvp_profile). `flops` and `bytes`
@@ -236,7 +248,18 @@ struct TcProblem {
   void* C;
   int64_t ldc;
   int c_fp64;
+  // K-split: the K range is cut into chunks of kchunk elements (a multiple of
+  // 32; 0 = no split), each chunk's product is accumulated in FP32 into its own
+  // partial tile part[chunk][M][N], and the partials are summed in FP64 into C.
+  // FP32 accumulation error grows with the number of terms; the split bounds
+  // it by the chunk length.
+  float* part = nullptr;
+  int kchunk = 0;
 };
+// Chooses the K-split of q for a partial buffer of cap floats: chunks of at
+// least TC_KCHUNK_MIN elements, as few as fit; no split for short K.
+constexpr int TC_KCHUNK_MIN = 512;
+void tc_set_ksplit(TcProblem& q, float* part, int64_t cap);
 void launch_tc_gemm(const std::vector<TcProblem>& probs, int passes, int* d_status, cudaStream_t s);
 bool tc_available();
 
@@ -280,5 +303,8 @@ struct SchedOp {
   int boundary, stage;
 };
 void build_half(int N, const std::vector<int>& seg_len, int half, int merge, std::vector<SchedOp>& ops);
+// segmented one-site step: kind 0 = site forward, 1 / 2 = bond backward with the
+// centre moving right / left, 3 = boundary pair (boundary = 1)
+void build_half1(int N, const std::vector<int>& seg_len, int half, int merge, std::vector<SchedOp>& ops);
 
 }  // namespace tdvp

@@ -105,6 +105,10 @@ void env_batch(int side, const std::vector<EnvProb>& P, const Ctx& c);
 // R as embedded B operand [2b][pad4(2 m b)] (hi, and lo when passes == 3).
 int64_t pad4(int64_t x);
 int64_t mixed_cap_floats(int chi, int m, int d);
+// environment updates of the mixed modes: double-float (default) or the
+// mode's tensor-core products
+void set_env_on_tensor_cores(bool on);
+bool env_on_tensor_cores();
 struct EnvFormJob {
   const double2* env;
   int chi, m;

@@ -13,41 +13,47 @@ namespace tdvp {
 // Complex FP64 GEMM. 64x64 output tile per 256-thread block, 8-deep K steps,
 // 4x4 outputs per thread. FP64 throughput, not memory, bounds this kernel.
 // ---------------------------------------------------------------------------
-constexpr int ZG_BM = 64, ZG_BN = 64, ZG_BK = 8;
+constexpr int ZG_BK = 8;
 
+// TT outputs per thread along each side: a (16 TT) x (16 TT) tile per CTA of
+// 256 threads. Every tile size sums each output over k in the same order, so
+// the results are bitwise the same; the autotuner picks one per shape.
+template <int TT>
 __global__ void __launch_bounds__(256) zgemm_kernel(const __grid_constant__ ZGemmBatch batch) {
+  constexpr int BM = 16 * TT, BN = 16 * TT;
   const int pid = blockIdx.y;
   if (pid >= batch.n) return;
   const ZGemmDesc& P = batch.d[pid];
   if (P.skip && *P.skip) return;
-  const int tiles_m = (P.M + ZG_BM - 1) / ZG_BM;
-  const int tiles_n = (P.N + ZG_BN - 1) / ZG_BN;
+  const int tiles_m = (P.M + BM - 1) / BM;
+  const int tiles_n = (P.N + BN - 1) / BN;
   if ((int)blockIdx.x >= tiles_m * tiles_n) return;
   const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
-  if (P.upper_only && tm > tn) return;
-  const int m0 = tm * ZG_BM, n0 = tn * ZG_BN;
-  __shared__ double2 As[ZG_BK][ZG_BM];
-  __shared__ double2 Bs[ZG_BK][ZG_BN];
+  const int m0 = tm * BM, n0 = tn * BN;
+  // Hermitian results: the blocks of 64 on or above the diagonal (any tile size)
+  if (P.upper_only && m0 / 64 > n0 / 64) return;
+  __shared__ double2 As[ZG_BK][BM];
+  __shared__ double2 Bs[ZG_BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  double2 acc[4][4];
+  double2 acc[TT][TT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < TT; ++j) acc[i][j] = make_double2(0.0, 0.0);
   const bool a_k_fast = (P.a_cs == 1);
   const bool b_n_fast = (P.b_cs == 1);
   for (int k0 = 0; k0 < P.K; k0 += ZG_BK) {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      int e = tid + r * 256;  // 0..511
+    for (int r = 0; r < ZG_BK * BM / 256; ++r) {
+      int e = tid + r * 256;
       int i, k;
       if (a_k_fast) {
         k = e % ZG_BK;
         i = e / ZG_BK;
       } else {
-        i = e % ZG_BM;
-        k = e / ZG_BM;
+        i = e % BM;
+        k = e / BM;
       }
       double2 v = make_double2(0.0, 0.0);
       int gi = m0 + i, gk = k0 + k;
@@ -63,8 +69,8 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const __grid_constant__ ZGem
       As[k][i] = v;
       int j, kb;
       if (b_n_fast) {
-        j = e % ZG_BN;
-        kb = e / ZG_BN;
+        j = e % BN;
+        kb = e / BN;
       } else {
         kb = e % ZG_BK;
         j = e / ZG_BK;
@@ -80,24 +86,24 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const __grid_constant__ ZGem
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < ZG_BK; ++kk) {
-      double2 a[4], b[4];
+      double2 a[TT], b[TT];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TT; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TT; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) zfma(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < TT; ++j) zfma(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TT; ++i) {
     int gi = m0 + ty + 16 * i;
     if (gi >= P.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TT; ++j) {
       int gj = n0 + tx + 16 * j;
       if (gj >= P.N) continue;
       double2* c = P.C + (int64_t)gi * P.c_rs + (int64_t)gj * P.c_cs;
@@ -108,26 +114,47 @@ __global__ void __launch_bounds__(256) zgemm_kernel(const __grid_constant__ ZGem
   }
 }
 
+// the largest M, N, K of a batch and whether any problem accumulates into C
+static void batch_shape(const ZGemmBatch& b, int64_t& M, int64_t& N, int64_t& K, bool& acc) {
+  M = N = K = 0;
+  acc = false;
+  for (int i = 0; i < b.n; ++i) {
+    M = std::max<int64_t>(M, b.d[i].M);
+    N = std::max<int64_t>(N, b.d[i].N);
+    K = std::max<int64_t>(K, b.d[i].K);
+    acc = acc || b.d[i].accumulate;
+  }
+}
+
 void launch_zgemm(const ZGemmBatch& b, cudaStream_t s, const char* prof_name) {
   if (b.n <= 0) return;
-  int maxt = 0;
-  for (int i = 0; i < b.n; ++i) {
-    const auto& d = b.d[i];
-    if (d.M <= 0 || d.N <= 0) continue;
-    maxt = std::max(maxt, cdiv(d.M, ZG_BM) * cdiv(d.N, ZG_BN));
-  }
-  if (maxt == 0) return;
+  int64_t M, N, K;
+  bool acc;
+  batch_shape(b, M, N, K, acc);
+  if (M <= 0 || N <= 0) return;
   double fl = 0, by = 0;
   for (int i = 0; i < b.n; ++i) {
     const auto& d = b.d[i];
     fl += (d.upper_only ? 4.0 : 8.0) * d.M * d.N * d.K;
     by += 16.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
   }
-  ProfScope ps(prof_name, s, fl, by);
-  dim3 grid(maxt, b.n);
-  zgemm_kernel<<<grid, 256, 0, s>>>(b);
-  LAUNCH_CHECK();
-  ++g_launches;
+  auto run = [&](int c) {
+    const int bm = c == 0 ? 64 : 32;
+    int maxt = 0;
+    for (int i = 0; i < b.n; ++i) {
+      const auto& d = b.d[i];
+      if (d.M <= 0 || d.N <= 0) continue;
+      maxt = std::max(maxt, cdiv(d.M, bm) * cdiv(d.N, bm));
+    }
+    ProfScope ps(prof_name, s, fl, by);
+    dim3 grid(maxt, b.n);
+    if (c == 0) zgemm_kernel<4><<<grid, 256, 0, s>>>(b);
+    else zgemm_kernel<2><<<grid, 256, 0, s>>>(b);
+    LAUNCH_CHECK();
+    ++g_launches;
+  };
+  if (!tune_enabled()) run(0);
+  else tune_pick(TUNE_ZGEMM, M, N, K, b.n, 2, !acc, run, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -245,30 +272,40 @@ __global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ Z
 
 void launch_zgemm_dd(const ZGemmBatch& b, cudaStream_t s, const char* prof_name) {
   if (b.n <= 0) return;
-  // 64 x 64 tiles when the batch fills the GPU, else 32 x 32 (4x the CTAs)
-  int64_t tiles64 = 0;
-  for (int i = 0; i < b.n; ++i) tiles64 += (int64_t)cdiv(b.d[i].M, 64) * cdiv(b.d[i].N, 64);
-  const int tt = tiles64 >= 2 * 152 ? 4 : 2;
-  const int bm = 16 * tt;
-  int maxt = 0;
-  for (int i = 0; i < b.n; ++i) {
-    const auto& d = b.d[i];
-    if (d.M <= 0 || d.N <= 0) continue;
-    maxt = std::max(maxt, cdiv(d.M, bm) * cdiv(d.N, bm));
-  }
-  if (maxt == 0) return;
+  int64_t M, N, K;
+  bool acc;
+  batch_shape(b, M, N, K, acc);
+  if (M <= 0 || N <= 0) return;
   double fl = 0, by = 0;
   for (int i = 0; i < b.n; ++i) {
     const auto& d = b.d[i];
     fl += (d.upper_only ? 4.0 : 8.0) * d.M * d.N * d.K;
     by += 16.0 * ((double)d.M * d.K + (double)d.K * d.N + (double)d.M * d.N);
   }
-  ProfScope ps(prof_name, s, fl, by);
-  dim3 grid(maxt, b.n);
-  if (tt == 4) zgemm_dd_kernel<4><<<grid, 256, 0, s>>>(b);
-  else zgemm_dd_kernel<2><<<grid, 256, 0, s>>>(b);
-  LAUNCH_CHECK();
-  ++g_launches;
+  auto run = [&](int c) {
+    const int tt = c == 0 ? 4 : 2;
+    const int bm = 16 * tt;
+    int maxt = 0;
+    for (int i = 0; i < b.n; ++i) {
+      const auto& d = b.d[i];
+      if (d.M <= 0 || d.N <= 0) continue;
+      maxt = std::max(maxt, cdiv(d.M, bm) * cdiv(d.N, bm));
+    }
+    ProfScope ps(prof_name, s, fl, by);
+    dim3 grid(maxt, b.n);
+    if (tt == 4) zgemm_dd_kernel<4><<<grid, 256, 0, s>>>(b);
+    else zgemm_dd_kernel<2><<<grid, 256, 0, s>>>(b);
+    LAUNCH_CHECK();
+    ++g_launches;
+  };
+  if (!tune_enabled()) {
+    // fixed rule: 64 x 64 tiles when the batch fills the GPU, else 32 x 32 (4x the CTAs)
+    int64_t tiles64 = 0;
+    for (int i = 0; i < b.n; ++i) tiles64 += (int64_t)cdiv(b.d[i].M, 64) * cdiv(b.d[i].N, 64);
+    run(tiles64 >= 2 * 152 ? 0 : 1);
+  } else {
+    tune_pick(TUNE_ZGEMM_DD, M, N, K, b.n, 2, !acc, run, s);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -7,6 +7,7 @@
 //   W      T2[(a S)][(w' b')] = sum_{w,S'} W[w,w',S,S'] T1[a,w,S',b']     chi^2 m^2 D^2 (sparse)
 //   GEMM2  y[(a S)][b]        = sum_(w' b') T2[(a S)][(w' b')] R[b][(w' b')]  chi^3 m D
 // with D = d^2 and W = W_j W_{j+1} (merged on the host) for two sites, D = d for one.
+#include <atomic>
 #include <algorithm>
 
 #include <mutex>
@@ -395,6 +396,8 @@ void matvec_batch(const std::vector<MvProb>& P, const std::vector<const double2*
     h.C = y[i];
     h.ldc = 2 * (int64_t)B;
     h.c_fp64 = 1;
+    // K = 2 m B terms: split, partial tiles in the T1 buffer (consumed by the W stage)
+    tc_set_ksplit(h, sl->f[2], sl->cap_f);
   }
   launch_prep(pb, c.s);
   launch_tc_gemm(t1, passes, c.d_status, c.s);
@@ -448,7 +451,9 @@ void expm_batch(const std::vector<MvProb>& P0, const std::vector<const double2*>
 // ---------------------------------------------------------------------------
 // Environment updates (Fig. 3, Eq. 19 and its mirror image)
 // ---------------------------------------------------------------------------
-static void env_fp64(int side, const std::vector<EnvProb>& P, const Ctx& c) {
+// dd: the two GEMMs in double-float on the FP32 pipe (~48 significant bits)
+// instead of FP64, the W stage in FP64 as on the FP64 path
+static void env_fp64(int side, const std::vector<EnvProb>& P, const Ctx& c, bool dd = false) {
   const int n = (int)P.size();
   ZGemmBatch g1{}, g3{};
   WStageBatch<double2> ws{};
@@ -548,9 +553,15 @@ static void env_fp64(int side, const std::vector<EnvProb>& P, const Ctx& c) {
     }
     b.accumulate = q.accumulate;
   }
-  launch_zgemm(g1, c.s);
-  launch_wstage(ws, c.s);
-  launch_zgemm(g3, c.s);
+  if (dd) {
+    launch_zgemm_dd(g1, c.s, "env_zgemm_dd");
+    launch_wstage(ws, c.s);
+    launch_zgemm_dd(g3, c.s, "env_zgemm_dd");
+  } else {
+    launch_zgemm(g1, c.s);
+    launch_wstage(ws, c.s);
+    launch_zgemm(g3, c.s);
+  }
 }
 
 static void env_tc(int side, const std::vector<EnvProb>& P, const Ctx& c) {
@@ -635,6 +646,7 @@ static void env_tc(int side, const std::vector<EnvProb>& P, const Ctx& c) {
       t3[i] = TcProblem{nullptr, TcOperand{x2.hi, x2.lo, B, 2 * A * d, x2.ld},
                         TcOperand{x3.hi, x3.lo, 2 * m * B, 2 * A * d, x3.ld}, B, 2 * m * B, 2 * A * d,
                         q.out, 2 * (int64_t)m * B, 1};
+      tc_set_ksplit(t3[i], sl->f[4], sl->cap_f);  // X1 buffer, consumed by the W stage
     } else {
       // GEMM1: A op = mat [(a' s')][b'], B op = env embedded: element (n=(b w'), k=b') at env[n B + k]
       x0.src = q.mat;
@@ -687,6 +699,7 @@ static void env_tc(int side, const std::vector<EnvProb>& P, const Ctx& c) {
       t3[i] = TcProblem{nullptr, TcOperand{x2.hi, x2.lo, A, 2 * d * B, x2.ld},
                         TcOperand{x3.hi, x3.lo, 2 * m * A, 2 * d * B, x3.ld}, A, 2 * m * A, 2 * d * B,
                         q.out, 2 * (int64_t)m * A, 1};
+      tc_set_ksplit(t3[i], sl->f[4], sl->cap_f);  // Y1 buffer, consumed by the W stage
     }
   }
   launch_prep(pa, c.s);
@@ -698,14 +711,29 @@ static void env_tc(int side, const std::vector<EnvProb>& P, const Ctx& c) {
   launch_tc_gemm(t3, passes, c.d_status, c.s);
 }
 
+namespace {
+std::atomic<int> g_env_tc{0};
+}
+
+void set_env_on_tensor_cores(bool on) { g_env_tc = on ? 1 : 0; }
+bool env_on_tensor_cores() { return g_env_tc.load() != 0; }
+
+// Mixed modes update the environments in double-float by default: they are
+// reused by every later H_eff of the half sweep, so their error acts like a
+// fixed perturbation of H and moves observables linearly in time; on the
+// tensor cores (FP32 accumulation) that drift was ~30x that of the
+// double-float environments at chi = 64.
 void env_batch(int side, const std::vector<EnvProb>& P, const Ctx& c) {
   if (P.empty()) return;
   if ((int)P.size() > MAXB) fail(TDVP_EINVAL, "batch too large");
-  if (c.prec != TDVP_FP64)
-    for (const auto& q : P)
-      if (q.bra || q.accumulate) fail(TDVP_EINVAL, "mixed bra/ket and accumulating environments are FP64 only");
-  if (c.prec == TDVP_FP64) env_fp64(side, P, c);
-  else env_tc(side, P, c);
+  if (c.prec == TDVP_FP64) {
+    env_fp64(side, P, c);
+    return;
+  }
+  for (const auto& q : P)
+    if (q.bra || q.accumulate) fail(TDVP_EINVAL, "mixed bra/ket and accumulating environments are FP64 only");
+  if (env_on_tensor_cores()) env_tc(side, P, c);
+  else env_fp64(side, P, c, true);
 }
 
 }  // namespace tdvp

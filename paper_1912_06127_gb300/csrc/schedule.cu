@@ -116,3 +116,89 @@ void build_half(int N, const std::vector<int>& seg_len, int half, int merge,
 }
 
 }  // namespace tdvp
+
+namespace tdvp {
+
+// Segmented one-site time step (the paper's outlook on a parallel one-site
+// TDVP, read as the one-site sweep inside every segment with the two-site
+// scheme's boundary pairs): op kinds 0 = one-site forward step on site j,
+// 1 = bond j evolved backward with the centre moving right (site j split,
+// its bond matrix carried into site j + 1), 2 = bond j - 1 evolved backward
+// with the centre moving left (site j split, carried into site j - 1),
+// 3 = the boundary pair (j, j + 1) evolved forward and split back at the
+// bond's current dimension. Directions, waits and turning rules are those of
+// build_half; a boundary site has its forward step inside the pair step, so a
+// segment leaving a boundary starts with the bond next to it. One segment
+// gives the serial one-site sweep.
+void build_half1(int N, const std::vector<int>& seg_len, int half, int merge, std::vector<SchedOp>& out) {
+  const int p = (int)seg_len.size();
+  std::vector<std::pair<int, int>> b(p);
+  int s0 = 0;
+  for (int k = 0; k < p; ++k) {
+    if (seg_len[k] < 2) fail(TDVP_EINVAL, "every segment needs at least two sites");
+    b[k] = {s0, s0 + seg_len[k] - 1};
+    s0 += seg_len[k];
+  }
+  if (s0 != N) fail(TDVP_EINVAL, "segment lengths do not add up to N");
+  const int turn = (half == 1 && merge) ? 2 : 1;
+  std::vector<std::vector<SchedOp>> q(p);
+  std::map<int, int> start_boundary, end_boundary;
+  auto op = [](int k, int kind, int j, int tf) { return SchedOp{k, kind, j, tf, 0, kind == 3 ? 1 : 0, -1}; };
+  for (int k = 0; k < p; ++k) {
+    const int s = b[k].first, e = b[k].second;
+    bool right = right_first(k, p);
+    if (half == 2) right = !right;
+    auto& Q = q[k];
+    if (right) {
+      if (s == 0 && (half == 1 || !merge)) Q.push_back(op(k, 0, 0, 1));
+      const int last_site = e == N - 1 ? e : e - 1;
+      for (int j = s; j < e; ++j) {
+        Q.push_back(op(k, 1, j, 1));
+        if (j + 1 <= last_site) Q.push_back(op(k, 0, j + 1, (j + 1 == e && e == N - 1) ? turn : 1));
+      }
+      if (e < N - 1) {
+        Q.push_back(op(k, 3, e, turn));
+        end_boundary[k] = (int)Q.size() - 1;
+      }
+    } else {
+      if (e == N - 1) {
+        if (half == 1 || !merge) Q.push_back(op(k, 0, N - 1, 1));
+      } else if (half == 1 || !merge) {
+        Q.push_back(op(k, 3, e, 1));
+        start_boundary[k] = (int)Q.size() - 1;
+      }
+      const int first_site = s == 0 ? s : s + 1;
+      for (int j = e; j > s; --j) {
+        Q.push_back(op(k, 2, j, 1));
+        if (j - 1 >= first_site) Q.push_back(op(k, 0, j - 1, (j - 1 == s && s == 0) ? turn : 1));
+      }
+    }
+  }
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int k = 0; k < p; ++k) {
+      int prev = -1;
+      for (size_t i = 0; i < q[k].size(); ++i) {
+        int st = prev + 1;
+        if (i == 0 && start_boundary.count(k - 1))
+          st = std::max(st, q[k - 1][start_boundary[k - 1]].stage + 1);
+        auto eb = end_boundary.find(k);
+        if (eb != end_boundary.end() && (int)i == eb->second) st = std::max(st, q[k + 1].back().stage + 1);
+        if (st != q[k][i].stage) {
+          q[k][i].stage = st;
+          changed = true;
+        }
+        prev = q[k][i].stage;
+      }
+    }
+  }
+  out.clear();
+  for (int k = 0; k < p; ++k)
+    for (auto& o : q[k]) out.push_back(o);
+  std::stable_sort(out.begin(), out.end(), [](const SchedOp& a, const SchedOp& c) {
+    return a.stage != c.stage ? a.stage < c.stage : a.seg < c.seg;
+  });
+}
+
+}  // namespace tdvp

@@ -24,14 +24,19 @@
 namespace tdvp {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BN = 256;
+// N tile: 256 (default) or 128 (twice the CTAs for small batches); chosen per
+// shape by the autotuner (tune.cu). Every column of a tile sums over K in the
+// same MMA order whatever the tile width, so both give the same result.
+template <int BN>
+struct TcTile {
+  static constexpr int B_BYTES = BN * 32 * 4;
+  static constexpr int STAGE_BYTES = 128 * 32 * 4 + B_BYTES;
+  static constexpr int SMEM = 4 * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int TMEM_COLS = BN;
+};
 constexpr int TC_BK = 32;  // fp32 elements = 128 bytes (one swizzle row)
 constexpr int TC_STAGES = 4;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;  // 16 KB
-constexpr int TC_B_BYTES = TC_BN * TC_BK * 4;  // 32 KB
-constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int TC_TMEM_COLS = 256;
 constexpr int TC_MAXP = 16;
 constexpr long long TC_SPIN_LIMIT = 1ll << 22;
 
@@ -43,6 +48,9 @@ struct TcParams {
   const int* skip[TC_MAXP];
   long long ldc[TC_MAXP];
   int c_fp64[TC_MAXP];
+  float* part[TC_MAXP];  // K-split partial tiles [chunk][M][N] (nch > 1)
+  int kcb[TC_MAXP];      // K blocks (of TC_BK) per chunk
+  int nch[TC_MAXP];      // chunks (1: no split)
   int n, passes;
   int* status;
 };
@@ -97,15 +105,21 @@ __host__ __device__ constexpr uint32_t tc_idesc(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+template <int TC_BN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ TcParams P) {
+  constexpr int TC_STAGE_BYTES = TcTile<TC_BN>::STAGE_BYTES;
+  constexpr int TC_TMEM_COLS = TcTile<TC_BN>::TMEM_COLS;
+  static_assert(TC_STAGES == 4 && TC_A_BYTES + TcTile<TC_BN>::B_BYTES == TC_STAGE_BYTES, "stage layout");
   const int pid = blockIdx.y;
   if (pid >= P.n) return;
   if (P.skip[pid] && *P.skip[pid]) return;
   const int M = P.M[pid], N = P.N[pid], K = P.K[pid];
   const int tiles_m = (M + TC_BM - 1) / TC_BM;
   const int tiles_n = (N + TC_BN - 1) / TC_BN;
-  if ((int)blockIdx.x >= tiles_m * tiles_n) return;
-  const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  const int tiles = tiles_m * tiles_n, nch = P.nch[pid];
+  if ((int)blockIdx.x >= tiles * nch) return;
+  const int tile = blockIdx.x % tiles, chunk = blockIdx.x / tiles;
+  const int tm = tile % tiles_m, tn = tile / tiles_m;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -135,7 +149,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  const int kb_per_pass = (K + TC_BK - 1) / TC_BK;
+  // this CTA's K blocks: [kb_lo, kb_lo + kb_per_pass) of every pass
+  const int kb_total = (K + TC_BK - 1) / TC_BK;
+  const int kb_lo = nch > 1 ? chunk * P.kcb[pid] : 0;
+  const int kb_per_pass = nch > 1 ? min(kb_total, kb_lo + P.kcb[pid]) - kb_lo : kb_total;
   const int num_kb = kb_per_pass * P.passes;
   const CUtensorMap* mA[3];
   const CUtensorMap* mB[3];
@@ -163,7 +180,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         }
       }
       const int pass = kb / kb_per_pass;
-      const int k0 = (kb % kb_per_pass) * TC_BK;
+      const int k0 = (kb_lo + kb % kb_per_pass) * TC_BK;
       uint8_t* sa = smem + s * TC_STAGE_BYTES;
       uint8_t* sb = sa + TC_A_BYTES;
       mbar_expect_tx(&full[s], TC_STAGE_BYTES);
@@ -232,7 +249,9 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (!row_ok) continue;
       const int col0 = tn * TC_BN + c0;
-      if (P.c_fp64[pid]) {
+      // K-split: this chunk's FP32 partial tile, summed in FP64 by tc_reduce_kernel
+      const bool split = nch > 1;
+      if (!split && P.c_fp64[pid]) {
         double* crow = (double*)P.C[pid] + (long long)row * P.ldc[pid];
         if (col0 + 32 <= N) {
 #pragma unroll
@@ -243,7 +262,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
           for (int i = 0; i < 32 && col0 + i < N; ++i) crow[col0 + i] = (double)__uint_as_float(r[i]);
         }
       } else {
-        float* crow = (float*)P.C[pid] + (long long)row * P.ldc[pid];
+        float* crow = split ? P.part[pid] + ((long long)chunk * M + row) * N
+                            : (float*)P.C[pid] + (long long)row * P.ldc[pid];
         if (col0 + 32 <= N) {
 #pragma unroll
           for (int i = 0; i < 32; i += 2)
@@ -259,6 +279,49 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
   }
+}
+
+// FP64 sum of the K-split partial tiles: C[row][col] = sum_chunk part[chunk][row][col].
+struct TcReduce {
+  const float* part[TC_MAXP];
+  void* C[TC_MAXP];
+  const int* skip[TC_MAXP];
+  long long ldc[TC_MAXP];
+  int M[TC_MAXP], N[TC_MAXP], nch[TC_MAXP], c_fp64[TC_MAXP];
+  int n;
+};
+
+__global__ void __launch_bounds__(256) tc_reduce_kernel(const __grid_constant__ TcReduce R) {
+  const int pid = blockIdx.y;
+  if (pid >= R.n) return;
+  if (R.skip[pid] && *R.skip[pid]) return;
+  const int N = R.N[pid], nch = R.nch[pid];
+  const long long MN = (long long)R.M[pid] * N;
+  const float* part = R.part[pid];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (long long)gridDim.x * blockDim.x) {
+    double sum = 0.0;
+    for (int c = 0; c < nch; ++c) sum += (double)part[c * MN + e];
+    const long long row = e / N, col = e - row * N;
+    if (R.c_fp64[pid]) ((double*)R.C[pid])[row * R.ldc[pid] + col] = sum;
+    else ((float*)R.C[pid])[row * R.ldc[pid] + col] = (float)sum;
+  }
+}
+
+void tc_set_ksplit(TcProblem& q, float* part, int64_t cap) {
+  q.part = nullptr;
+  q.kchunk = 0;
+  if (!part || q.K <= TC_KCHUNK_MIN || (q.N & 1)) return;
+  const int64_t tile = (int64_t)q.M * q.N;
+  const int64_t fit = tile > 0 ? cap / tile : 0;
+  if (fit < 2) return;
+  // chunks of at least TC_KCHUNK_MIN, as many as the buffer holds
+  int nch = (q.K + TC_KCHUNK_MIN - 1) / TC_KCHUNK_MIN;
+  if (nch > fit) nch = (int)fit;
+  int kc = (q.K + nch - 1) / nch;
+  kc = (kc + TC_BK - 1) / TC_BK * TC_BK;
+  if (kc >= q.K) return;
+  q.part = part;
+  q.kchunk = kc;
 }
 
 // ---------------------------------------------------------------------------
@@ -296,31 +359,33 @@ static void encode_map(CUtensorMap* map, const float* base, int rows, int k, int
   if (r != CUDA_SUCCESS) fail(TDVP_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
-void launch_tc_gemm(const std::vector<TcProblem>& probs, int passes, int* d_status, cudaStream_t s) {
-  if (probs.empty()) return;
-  load_encode();
-  if (!g_encode) fail(TDVP_ECUDA, "cuTensorMapEncodeTiled unavailable");
+// One launch of the problems [base, end) (at most TC_MAXP) with N tile BN, then
+// the FP64 sum of their K-split partial tiles.
+template <int BN>
+static void tc_launch_range(const std::vector<TcProblem>& probs, size_t base, size_t end, int passes,
+                            int* d_status, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  TcTile<BN>::SMEM));
     attr_set = true;
   }
-  for (size_t base = 0; base < probs.size(); base += TC_MAXP) {
+  {
     TcParams* P = new TcParams();
     std::unique_ptr<TcParams> guard(P);
     P->n = 0;
     P->passes = passes;
     P->status = d_status;
     int max_tiles = 0;
-    for (size_t i = base; i < probs.size() && P->n < TC_MAXP; ++i) {
+    for (size_t i = base; i < end; ++i) {
       const TcProblem& q = probs[i];
       if (q.M <= 0 || q.N <= 0 || q.K <= 0) continue;
       const int n = P->n;
       encode_map(&P->mapA[n][0], q.A.hi, q.A.rows, q.A.k, q.A.ld, TC_BM);
-      encode_map(&P->mapB[n][0], q.B.hi, q.B.rows, q.B.k, q.B.ld, TC_BN);
+      encode_map(&P->mapB[n][0], q.B.hi, q.B.rows, q.B.k, q.B.ld, BN);
       if (passes == 3) {
         encode_map(&P->mapA[n][1], q.A.lo, q.A.rows, q.A.k, q.A.ld, TC_BM);
-        encode_map(&P->mapB[n][1], q.B.lo, q.B.rows, q.B.k, q.B.ld, TC_BN);
+        encode_map(&P->mapB[n][1], q.B.lo, q.B.rows, q.B.k, q.B.ld, BN);
       } else {
         P->mapA[n][1] = P->mapA[n][0];
         P->mapB[n][1] = P->mapB[n][0];
@@ -332,20 +397,80 @@ void launch_tc_gemm(const std::vector<TcProblem>& probs, int passes, int* d_stat
       P->skip[n] = q.skip;
       P->ldc[n] = q.ldc;
       P->c_fp64[n] = q.c_fp64;
-      max_tiles = std::max(max_tiles, cdiv(q.M, TC_BM) * cdiv(q.N, TC_BN));
+      const bool split = q.part && q.kchunk > 0 && q.kchunk < q.K && q.kchunk % TC_BK == 0;
+      P->part[n] = split ? q.part : nullptr;
+      P->kcb[n] = split ? q.kchunk / TC_BK : 0;
+      P->nch[n] = split ? cdiv(q.K, q.kchunk) : 1;
+      max_tiles = std::max(max_tiles, cdiv(q.M, TC_BM) * cdiv(q.N, BN) * P->nch[n]);
       ++P->n;
     }
-    if (P->n == 0) continue;
-    double fl = 0, by = 0;
+    if (P->n == 0) return;
+    double fl = 0, by = 0, by_red = 0;
+    bool any_split = false;
     for (int i = 0; i < P->n; ++i) {
-      fl += 2.0 * P->M[i] * (double)P->N[i] * P->K[i];
-      by += 4.0 * ((double)P->M[i] + P->N[i]) * P->K[i] * passes + (P->c_fp64[i] ? 8.0 : 4.0) * P->M[i] * P->N[i];
+      const double mn = (double)P->M[i] * P->N[i];
+      fl += 2.0 * mn * P->K[i];
+      by += 4.0 * ((double)P->M[i] + P->N[i]) * P->K[i] * passes;
+      if (P->nch[i] > 1) {
+        any_split = true;
+        by += 4.0 * mn * P->nch[i];
+        by_red += (4.0 * P->nch[i] + (P->c_fp64[i] ? 8.0 : 4.0)) * mn;
+      } else {
+        by += (P->c_fp64[i] ? 8.0 : 4.0) * mn;
+      }
     }
-    ProfScope ps(passes == 3 ? "tc_gemm_tf32x3" : "tc_gemm_tf32", s, fl, by);
-    dim3 grid(max_tiles, P->n);
-    tc_gemm_kernel<<<grid, 128, TC_SMEM, s>>>(*P);
-    LAUNCH_CHECK();
-    ++g_launches;
+    {
+      ProfScope ps(passes == 3 ? "tc_gemm_tf32x3" : "tc_gemm_tf32", s, fl, by);
+      dim3 grid(max_tiles, P->n);
+      tc_gemm_kernel<BN><<<grid, 128, TcTile<BN>::SMEM, s>>>(*P);
+      LAUNCH_CHECK();
+      ++g_launches;
+    }
+    if (any_split) {
+      TcReduce R{};
+      R.n = P->n;
+      int64_t max_mn = 0;
+      for (int i = 0; i < P->n; ++i) {
+        R.part[i] = P->part[i];
+        R.C[i] = P->C[i];
+        R.skip[i] = P->skip[i];
+        R.ldc[i] = P->ldc[i];
+        R.M[i] = P->M[i];
+        R.N[i] = P->N[i];
+        R.c_fp64[i] = P->c_fp64[i];
+        // problems without a split were written by the GEMM itself
+        R.nch[i] = P->nch[i];
+        if (P->nch[i] <= 1) R.M[i] = 0;
+        max_mn = std::max<int64_t>(max_mn, (int64_t)R.M[i] * R.N[i]);
+      }
+      ProfScope ps("tc_reduce", s, 0.0, by_red);
+      dim3 grid((unsigned)std::min<int64_t>(cdiv64(max_mn, 256), 152 * 4), R.n);
+      tc_reduce_kernel<<<grid, 256, 0, s>>>(R);
+      LAUNCH_CHECK();
+      ++g_launches;
+    }
+  }
+}
+
+
+void launch_tc_gemm(const std::vector<TcProblem>& probs, int passes, int* d_status, cudaStream_t s) {
+  if (probs.empty()) return;
+  load_encode();
+  if (!g_encode) fail(TDVP_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  for (size_t base = 0; base < probs.size(); base += TC_MAXP) {
+    const size_t end = std::min(probs.size(), base + (size_t)TC_MAXP);
+    int64_t M = 0, N = 0, K = 0;
+    for (size_t i = base; i < end; ++i) {
+      M = std::max<int64_t>(M, probs[i].M);
+      N = std::max<int64_t>(N, probs[i].N);
+      K = std::max<int64_t>(K, probs[i].K);
+    }
+    auto run = [&](int c) {
+      if (c == 0) tc_launch_range<256>(probs, base, end, passes, d_status, s);
+      else tc_launch_range<128>(probs, base, end, passes, d_status, s);
+    };
+    if (!tune_enabled()) run(0);
+    else tune_pick(passes == 3 ? TUNE_TC_TF32X3 : TUNE_TC_TF32, M, N, K, (int)(end - base), 2, true, run, s);
   }
 }
 

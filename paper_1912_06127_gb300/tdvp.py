@@ -125,11 +125,16 @@ def lib():
                            _P, _P, _P, _P, _I, _D, _P], ctypes.c_int),
         "tdvp_schedule": ([ctypes.c_int, ctypes.c_int, _I, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int],
                           ctypes.c_int),
+        "tdvp_schedule1": ([ctypes.c_int, ctypes.c_int, _I, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int],
+                           ctypes.c_int),
         "tdvp_tridiag_expm": ([ctypes.c_int, _D, _D, ctypes.c_double, _D], ctypes.c_int),
         "tdvp_profile": ([ctypes.c_int], ctypes.c_int),
         "tdvp_profile_read_aux": ([ctypes.c_int, _D], ctypes.c_int),
         "tdvp_op_heff_noalloc": ([ctypes.c_int] * 5 + [_D, _P, _P, _P, _P, _P], ctypes.c_int),
         "tdvp_set_wait_limit": ([ctypes.c_longlong], ctypes.c_int),
+        "tdvp_set_autotune": ([ctypes.c_int], ctypes.c_int),
+        "tdvp_set_env_tensor_cores": ([ctypes.c_int], ctypes.c_int),
+        "tdvp_autotune_report": ([ctypes.c_char_p, ctypes.c_int], ctypes.c_int),
         "tdvp_profile_read": ([ctypes.c_int, ctypes.c_char_p, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int64),
                                _D, _D], ctypes.c_int),
         "tdvp_build_mpo_derivative": ([_P, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
@@ -363,7 +368,7 @@ def step(mps: Mps, mpo: Mpo, params: StepParams, n_steps: int = 1, stream=None,
 
 def step1(mps: Mps, mpo: Mpo, params: StepParams, n_steps: int = 1, stream=None,
           stats: Optional[StepStats] = None) -> StepStats:
-    """One-site TDVP steps (serial, FP64, fixed bond dimension)."""
+    """One-site TDVP steps (FP64, fixed bond dimension; segmented when params has segments)."""
     st = stats if stats is not None else StepStats()
     _check(lib().tdvp_step1(mps.handle, mpo.handle, ctypes.byref(params), n_steps, ctypes.byref(st),
                             _stream(stream)))
@@ -540,12 +545,41 @@ def schedule(N: int, seg_len: Optional[Sequence[int]], merge_turning: int, half:
     return out
 
 
+def schedule1(N: int, seg_len: Optional[Sequence[int]], merge_turning: int, half: int) -> np.ndarray:
+    """Stage schedule of a segmented one-site half step (tdvp_schedule1)."""
+    seg = np.ascontiguousarray(seg_len if seg_len else [N], dtype=np.int32)
+    n = _check(lib().tdvp_schedule1(N, len(seg), seg.ctypes.data_as(_I), merge_turning, half, None, 0))
+    out = np.zeros((n, 7), dtype=np.int32)
+    _check(lib().tdvp_schedule1(N, len(seg), seg.ctypes.data_as(_I), merge_turning, half,
+                                out.ctypes.data_as(_I), n))
+    return out
+
+
 def tridiag_expm(alpha: np.ndarray, beta: np.ndarray, t: float) -> np.ndarray:
     a = np.ascontiguousarray(alpha, dtype=np.float64)
     b = np.ascontiguousarray(beta if len(beta) else [0.0], dtype=np.float64)
     out = _cplx_out(len(a))
     _check(lib().tdvp_tridiag_expm(len(a), _dptr(a), _dptr(b), t, _dptr(out.view(np.float64))))
     return out
+
+
+def set_env_tensor_cores(enable: bool) -> None:
+    """Mixed modes: environment updates on the tensor cores (True) or in double-float (False, default)."""
+    _check(lib().tdvp_set_env_tensor_cores(1 if enable else 0))
+
+
+def set_autotune(enable: bool) -> None:
+    """Per-shape GEMM tile autotuning on (default) or off (fixed tiles); clears the decisions."""
+    _check(lib().tdvp_set_autotune(1 if enable else 0))
+
+
+def autotune_report() -> list:
+    """The autotuner's decisions so far (family, shape bucket, choice, microseconds per candidate)."""
+    import json
+    n = _check(lib().tdvp_autotune_report(None, 0))
+    buf = ctypes.create_string_buffer(n + 1)
+    lib().tdvp_autotune_report(buf, n + 1)
+    return json.loads(buf.value.decode())
 
 
 def set_wait_limit(spins: int) -> None:

@@ -65,12 +65,20 @@ def test_heff_one_site(prec, kind, chi_l, chi_r):
     assert max_err(host(y).reshape(ref.shape), ref) < TOL[prec]
 
 
+ENV_TOL_DD = 1e-12  # mixed modes' default double-float environments (~48 bits)
+
+
+@pytest.mark.parametrize("env_tc", [False, True], ids=["env_dd", "env_tc"])
 @pytest.mark.parametrize("prec", [FP64, TF32, TF32X3], ids=["fp64", "tf32", "tf32x3"])
 @pytest.mark.parametrize("side", [0, 1])
 @pytest.mark.parametrize("chi_l,chi_r", [(1, 2), (2, 4), (7, 13), (64, 50), (128, 128)])
-def test_env_update(prec, side, chi_l, chi_r):
+def test_env_update(env_tc, prec, side, chi_l, chi_r):
+    """Environment updates: FP64; the mixed modes' default double-float GEMMs
+    (to ~1e-12); and, switched to the tensor cores, the mode's products."""
     torch = torch_or_skip()
     tdvp = lib()
+    if env_tc and prec == FP64:
+        pytest.skip("the FP64 path has one environment update")
     W = mpo_W(kind=models.XY, K=3)
     m, d = W.shape[0], 2
     A = I.random_complex((chi_l, d, chi_r), 7)
@@ -81,8 +89,13 @@ def test_env_update(prec, side, chi_l, chi_r):
         env = hermitian_env((chi_r, m, chi_r), 9)
         ref = T.env_right(env, A, W)
     out = torch.zeros(ref.size, dtype=torch.complex128, device="cuda")
-    tdvp.op_env(prec, side, chi_l, chi_r, m, d, W, dev(torch, env), dev(torch, A), out)
-    assert max_err(host(out).reshape(ref.shape), ref) < TOL[prec]
+    tdvp.set_env_tensor_cores(env_tc)
+    try:
+        tdvp.op_env(prec, side, chi_l, chi_r, m, d, W, dev(torch, env), dev(torch, A), out)
+    finally:
+        tdvp.set_env_tensor_cores(False)
+    tol = TOL[prec] if (env_tc or prec == FP64) else ENV_TOL_DD
+    assert max_err(host(out).reshape(ref.shape), ref) < tol
 
 
 @pytest.mark.parametrize("nsite", [1, 2])

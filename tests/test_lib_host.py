@@ -92,6 +92,22 @@ def test_schedule_matches_oracle(tdvp, seg, merge):
         assert np.array_equal(lib_ops, ref)
 
 
+@pytest.mark.parametrize("seg", [[10], [5, 5], [3, 3, 4], [2, 3, 3, 3], [2, 2, 2, 2, 2, 2], [13, 13, 13, 12],
+                                 [15, 12, 12, 12, 12, 12, 12, 14]])
+@pytest.mark.parametrize("merge", [0, 1])
+def test_one_site_schedule_matches_oracle(tdvp, seg, merge):
+    from oracle import tdvp1 as T1
+    N = sum(seg)
+    kinds = {"site": 0, "bond_r": 1, "bond_l": 2, "pair": 3}
+    for half in (1, 2):
+        lib_ops = tdvp.schedule1(N, seg, merge, half)
+        ora = T1.build_half1(N, seg, half, merge)
+        ref = np.array([[o.seg, kinds[o.kind], o.j, o.tfac, 0, int(o.kind == "pair"), o.stage] for o in ora],
+                       dtype=np.int32)
+        assert lib_ops.shape == ref.shape
+        assert np.array_equal(lib_ops, ref)
+
+
 def test_schedule_rejects_short_segment(tdvp):
     with pytest.raises(tdvp.TdvpError):
         tdvp.schedule(5, [1, 4], 1, 1)
