@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--precision", default="tf32x3", choices=sorted(PREC))
     ap.add_argument("--chi", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="steps of the plain FP64 GPU path, each timed, compared step by step with the "
                          "mixed path from the same state; 0 skips it")

@@ -163,7 +163,10 @@ def truncation_rank(s: np.ndarray, chi_max: int, w_max: float, eps: float) -> Tu
 
     chi_w = smallest rank with sum_{j >= chi_w} s_j^2 <= w_max (Eq. 22);
     chi = min(chi_w, chi_max) (Sec. III C), further limited to the values
-    above eps * s_0 (Sec. III D); at least one value is kept.
+    above eps * s_0 (Sec. III D) and to those above the FP64 rounding level
+    1e-14 * ||s||_2 (= ||Theta'||_F): values at the noise level are numerical
+    zeros, thrown away before Lambda is inverted (Sec. II B and its footnote),
+    whatever eps. At least one value is kept.
     """
     n = len(s)
     sq = s.astype(np.float64) ** 2
@@ -176,7 +179,8 @@ def truncation_rank(s: np.ndarray, chi_max: int, w_max: float, eps: float) -> Tu
             chi_w = k
             break
     n_eps = int(np.count_nonzero(s > eps * s[0])) if s[0] > 0 else 1
-    chi = max(1, min(chi_w, chi_max, n_eps))
+    n_noise = int(np.count_nonzero(s > 1e-14 * np.sqrt(sq.sum())))
+    chi = max(1, min(chi_w, chi_max, n_eps, n_noise))
     return chi, float(tail[chi])
 
 

@@ -315,6 +315,36 @@ void lz_orthogonalize(const LzBatch& b, int j, cudaStream_t s) {
   g_launches += 5;
 }
 
+// count of problems still iterating, written to host-mapped memory
+__global__ void lz_count_open(const __grid_constant__ LzBatch B, int* out) {
+  __shared__ int open;
+  if (threadIdx.x == 0) open = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < B.n; i += blockDim.x)
+    if (!B.d[i].st->done) atomicAdd(&open, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) *(volatile int*)out = open;
+}
+
+bool lz_all_done(const LzBatch& b, cudaStream_t s) {
+  thread_local int* h_open = nullptr;
+  thread_local int* d_open = nullptr;
+  thread_local int dev_of = -1;
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (!h_open || dev_of != dev) {
+    CUDA_TRY(cudaHostAlloc((void**)&h_open, sizeof(int), cudaHostAllocMapped));
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&d_open, h_open, 0));
+    dev_of = dev;
+  }
+  *h_open = 1;
+  lz_count_open<<<1, 64, 0, s>>>(b, d_open);
+  LAUNCH_CHECK();
+  ++g_launches;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return *(volatile int*)h_open == 0;
+}
+
 void lz_finish(const LzBatch& b, cudaStream_t s) {
   if (b.n <= 0) return;
   lz_combine<<<lz_grid(b, false), LZ_THREADS, 0, s>>>(b);

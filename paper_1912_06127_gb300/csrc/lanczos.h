@@ -28,5 +28,8 @@ void lz_start(const LzBatch& b, cudaStream_t s);
 // call after the matvec that wrote H v_j into slot j+1
 void lz_orthogonalize(const LzBatch& b, int j, cudaStream_t s);
 void lz_finish(const LzBatch& b, cudaStream_t s);
+// whether every problem of the batch has converged or broken down (one small
+// launch and a synchronisation of s)
+bool lz_all_done(const LzBatch& b, cudaStream_t s);
 
 }  // namespace tdvp

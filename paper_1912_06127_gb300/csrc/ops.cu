@@ -437,6 +437,13 @@ void expm_batch(const std::vector<MvProb>& P0, const std::vector<const double2*>
   lz_start(lb, c.s);
   std::vector<const double2*> xin(n);
   std::vector<double2*> yout(n);
+  // small batches are launch-bound: once every problem has converged (or its
+  // Krylov space is exhausted) the remaining iterations would only launch
+  // kernels that return at once, so the loop stops (a host check per
+  // iteration, from the third on; large batches keep launching instead)
+  int64_t n_all = 0;
+  for (int i = 0; i < n; ++i) n_all += lb.d[i].n;
+  const bool check = n_all <= (int64_t(1) << 20);
   for (int j = 0; j < kmax; ++j) {
     for (int i = 0; i < n; ++i) {
       xin[i] = lb.d[i].V + (int64_t)j * lb.d[i].vs;
@@ -444,6 +451,7 @@ void expm_batch(const std::vector<MvProb>& P0, const std::vector<const double2*>
     }
     matvec_batch(P, xin, yout, c);
     lz_orthogonalize(lb, j, c.s);
+    if (check && j >= 2 && j + 1 < kmax && lz_all_done(lb, c.s)) break;
   }
   lz_finish(lb, c.s);
 }

@@ -152,6 +152,13 @@ def test_truncation_rank_rules():
     assert T.truncation_rank(s, 10, 1e-13, 0.0)[0] == 3
     # at least one value is kept
     assert T.truncation_rank(np.array([0.0, 0.0]), 4, 1.0, 1e-12)[0] == 1
+    # numerical zeros (below 1e-14 of the norm) are dropped even at eps = 0,
+    # and their weight counts as discarded
+    s2 = np.array([1.0, 0.5, 2e-14, 5e-15, 0.0])
+    chi, w = T.truncation_rank(s2, 10, 0.0, 0.0)
+    assert chi == 3 and abs(w - 5e-15 ** 2) < 1e-40
+    chi, w = T.truncation_rank(np.array([1.0, 0.5, 1e-15]), 10, 0.0, 0.0)
+    assert chi == 2 and abs(w - 1e-30) < 1e-44
 
 
 def test_split_reconstructs_and_orders():
