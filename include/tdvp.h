@@ -530,6 +530,22 @@ int tdvp_schedule(int N, int n_seg, const int* seg_len, int merge_turning, int h
  * negative error code. */
 int tdvp_schedule1(int N, int n_seg, const int* seg_len, int merge_turning, int half, int* out, int max_ops);
 
+/* Point-to-point messages of one half step (1 or 2) when the segments are
+ * spread over ranks, one GPU each (Sec. III B: the segments were MPI
+ * processes exchanging O(chi^2 (m + d)) numbers at their boundaries).
+ * seg_rank[k]: rank of segment k, non-decreasing (contiguous groups). scheme:
+ * 2 = tdvp_step's schedule, 1 = tdvp_step1's. For every boundary update whose
+ * two segments live on different ranks: before it the right rank sends
+ * Psi_{e+1} and gamma_{e+1} to the left rank, after it the left rank sends
+ * Psi_{e+1}, V_e and beta_{e+1} back. 6 ints per message: stage of the
+ * boundary update, 0 = before / 1 = after it, source rank, destination rank,
+ * tensor (0 = Psi_j, 1 = V_j, 2 = beta_j, 3 = gamma_j), j. Ranks that run the
+ * stages in lockstep and exchange these messages reproduce the one-rank
+ * sweep. Returns the number of messages (out may be NULL to query it) or a
+ * negative error code. Host only. */
+int tdvp_exchange_plan(int N, int n_seg, const int* seg_len, const int* seg_rank, int scheme, int merge_turning,
+                       int half, int* out, int max_msgs);
+
 /* c = exp(-i t T) e_0 (2*k doubles) for the real symmetric tridiagonal T with
  * diagonal alpha[k] and off-diagonal beta[k-1] -- the small exponential of the
  * Lanczos method; the same routine runs inside the device kernels. k <= 24. */

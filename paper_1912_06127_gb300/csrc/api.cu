@@ -1493,6 +1493,35 @@ int tdvp_op_split_prec(int precision, int rows, int cols, const double* theta, i
   });
 }
 
+int tdvp_exchange_plan(int N, int n_seg, const int* seg_len, const int* seg_rank, int scheme, int merge_turning,
+                       int half, int* out, int max_msgs) {
+  int count = 0;
+  int rc = ok_or_code([&] {
+    if (half != 1 && half != 2) fail(TDVP_EINVAL, "half must be 1 or 2");
+    if (N < 2 || n_seg < 1 || !seg_len || !seg_rank) fail(TDVP_EINVAL, "invalid arguments");
+    std::vector<int> seg(seg_len, seg_len + n_seg), rk(seg_rank, seg_rank + n_seg);
+    for (int k = 0; k < n_seg; ++k)
+      if (rk[k] < 0 || (k > 0 && rk[k] < rk[k - 1])) fail(TDVP_EINVAL, "ranks must hold contiguous groups of segments");
+    std::vector<ExchangeMsg> msgs;
+    exchange_plan(N, seg, rk, scheme, merge_turning, half, msgs);
+    count = (int)msgs.size();
+    if (out) {
+      if (max_msgs < count) fail(TDVP_EINVAL, "output too small");
+      for (int i = 0; i < count; ++i) {
+        const ExchangeMsg& m = msgs[i];
+        int* r = out + 6 * i;
+        r[0] = m.stage;
+        r[1] = m.after;
+        r[2] = m.src;
+        r[3] = m.dst;
+        r[4] = m.kind;
+        r[5] = m.j;
+      }
+    }
+  });
+  return rc == TDVP_OK ? count : rc;
+}
+
 int tdvp_schedule1(int N, int n_seg, const int* seg_len, int merge_turning, int half, int* out, int max_ops) {
   int count = 0;
   int rc = ok_or_code([&] {

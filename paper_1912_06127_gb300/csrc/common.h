@@ -306,5 +306,13 @@ void build_half(int N, const std::vector<int>& seg_len, int half, int merge, std
 // segmented one-site step: kind 0 = site forward, 1 / 2 = bond backward with the
 // centre moving right / left, 3 = boundary pair (boundary = 1)
 void build_half1(int N, const std::vector<int>& seg_len, int half, int merge, std::vector<SchedOp>& ops);
+// point-to-point messages of a half step with the segments spread over ranks
+enum { XCH_PSI = 0, XCH_V = 1, XCH_BETA = 2, XCH_GAMMA = 3 };
+struct ExchangeMsg {
+  int stage, after;   // the boundary update's stage; 0 = before it, 1 = after it
+  int src, dst, kind, j;
+};
+void exchange_plan(int N, const std::vector<int>& seg_len, const std::vector<int>& seg_rank, int scheme,
+                   int merge, int half, std::vector<ExchangeMsg>& out);
 
 }  // namespace tdvp

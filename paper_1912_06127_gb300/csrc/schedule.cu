@@ -202,3 +202,38 @@ void build_half1(int N, const std::vector<int>& seg_len, int half, int merge, st
 }
 
 }  // namespace tdvp
+
+namespace tdvp {
+
+// Messages of one half step when the segments are spread over ranks (one GPU
+// each; the layout of the paper's Sec. III B: contiguous groups of segments
+// per rank). Every cross-segment read of the schedule happens at a boundary
+// update, executed by the left segment: before it the right rank sends its
+// current Psi_{e+1} and gamma_{e+1} to the left rank; after it the left rank
+// sends the new Psi_{e+1}, V_e and beta_{e+1} back (Sec. III B: O(chi^2 (m +
+// d)) numbers per boundary). Boundaries inside a rank exchange nothing. With
+// the ranks running the stages in lockstep this reproduces the one-rank
+// result: the right segment's last op of the half comes in an earlier stage
+// than the boundary update, and its next op in a later one.
+void exchange_plan(int N, const std::vector<int>& seg_len, const std::vector<int>& seg_rank, int scheme,
+                   int merge, int half, std::vector<ExchangeMsg>& out) {
+  if (seg_rank.size() != seg_len.size()) fail(TDVP_EINVAL, "one rank per segment");
+  std::vector<SchedOp> ops;
+  if (scheme == 2) build_half(N, seg_len, half, merge, ops);
+  else if (scheme == 1) build_half1(N, seg_len, half, merge, ops);
+  else fail(TDVP_EINVAL, "scheme must be 1 (one-site) or 2 (two-site)");
+  out.clear();
+  for (const SchedOp& o : ops) {
+    if (!o.boundary) continue;
+    const int left = seg_rank[o.seg], right = seg_rank[o.seg + 1];
+    if (left == right) continue;
+    const int e = o.j;
+    out.push_back(ExchangeMsg{o.stage, 0, right, left, XCH_PSI, e + 1});
+    out.push_back(ExchangeMsg{o.stage, 0, right, left, XCH_GAMMA, e + 1});
+    out.push_back(ExchangeMsg{o.stage, 1, left, right, XCH_PSI, e + 1});
+    out.push_back(ExchangeMsg{o.stage, 1, left, right, XCH_V, e});
+    out.push_back(ExchangeMsg{o.stage, 1, left, right, XCH_BETA, e + 1});
+  }
+}
+
+}  // namespace tdvp

@@ -127,6 +127,8 @@ def lib():
                           ctypes.c_int),
         "tdvp_schedule1": ([ctypes.c_int, ctypes.c_int, _I, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int],
                            ctypes.c_int),
+        "tdvp_exchange_plan": ([ctypes.c_int, ctypes.c_int, _I, _I, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I,
+                                ctypes.c_int], ctypes.c_int),
         "tdvp_tridiag_expm": ([ctypes.c_int, _D, _D, ctypes.c_double, _D], ctypes.c_int),
         "tdvp_profile": ([ctypes.c_int], ctypes.c_int),
         "tdvp_profile_read_aux": ([ctypes.c_int, _D], ctypes.c_int),
@@ -552,6 +554,20 @@ def schedule1(N: int, seg_len: Optional[Sequence[int]], merge_turning: int, half
     out = np.zeros((n, 7), dtype=np.int32)
     _check(lib().tdvp_schedule1(N, len(seg), seg.ctypes.data_as(_I), merge_turning, half,
                                 out.ctypes.data_as(_I), n))
+    return out
+
+
+def exchange_plan(N: int, seg_len: Sequence[int], seg_rank: Sequence[int], scheme: int, merge_turning: int,
+                  half: int) -> np.ndarray:
+    """Messages of a half step with the segments on several ranks (tdvp_exchange_plan):
+    rows (stage, after, src, dst, tensor, j), tensor 0 = Psi_j, 1 = V_j, 2 = beta_j, 3 = gamma_j."""
+    seg = np.ascontiguousarray(seg_len, dtype=np.int32)
+    rk = np.ascontiguousarray(seg_rank, dtype=np.int32)
+    n = _check(lib().tdvp_exchange_plan(N, len(seg), seg.ctypes.data_as(_I), rk.ctypes.data_as(_I), scheme,
+                                        merge_turning, half, None, 0))
+    out = np.zeros((n, 6), dtype=np.int32)
+    _check(lib().tdvp_exchange_plan(N, len(seg), seg.ctypes.data_as(_I), rk.ctypes.data_as(_I), scheme,
+                                    merge_turning, half, out.ctypes.data_as(_I), n))
     return out
 
 
