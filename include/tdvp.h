@@ -263,9 +263,10 @@ int tdvp_step(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_
  * stats->n_fwd2 the boundary pair updates. */
 int tdvp_step1(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps,
                tdvp_step_stats* stats, void* stream);
-/* The hybrid scheme: per step, a tdvp_step (two-site, any segmentation) while
- * some bond is below min(chi_max, its largest possible dimension), else a
- * tdvp_step1. FP64 only. Returns the number of one-site steps (>= 0) or an error. */
+/* The hybrid scheme: per step, a tdvp_step (two-site) while some bond is below
+ * min(chi_max, its largest possible dimension), else a tdvp_step1 (one-site),
+ * both with the segments of params (serial without). FP64 only. Returns the
+ * number of one-site steps (>= 0) or an error. */
 int tdvp_step_hybrid(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_steps,
                      tdvp_step_stats* stats, void* stream);
 

@@ -121,11 +121,12 @@ def saturated(eng: Engine, chi_max: int) -> bool:
 
 def step_hybrid(eng: Engine, p: Params, n_steps: int = 1) -> int:
     """The hybrid scheme: a two-site step while some bond can still grow, a one-site
-    step once all are saturated. Returns the number of one-site steps taken."""
+    step once all are saturated, both with the segments of p.seg_len (serial
+    without). Returns the number of one-site steps taken."""
     n1 = 0
     for _ in range(n_steps):
         if saturated(eng, p.chi_max):
-            step1(eng, p, 1)
+            step1_segmented(eng, p, 1)
             n1 += 1
         else:
             eng.step(p, 1)
@@ -259,14 +260,21 @@ def run_op1(eng: Engine, op: Op1, p: Params) -> None:
 
 def step1_segmented(eng: Engine, p: Params, n_steps: int = 1) -> None:
     """n_steps symmetric one-site steps with the segments of p.seg_len (one
-    segment: the serial sweep of step1). At the start of a step gamma_0 and
-    beta_{N-1} are rebuilt from the current state, as step1 does for gamma_0."""
+    segment: the serial sweep of step1). At the start of a step the chain-end
+    environment that the first half reads first is rebuilt from the current
+    state, as step1 does for gamma_0 (a two-site half that ends moving away
+    from a chain end leaves that end's environment behind): gamma_0 when the
+    first segment starts at site 0, beta_{N-1} when the last one starts at
+    site N-1."""
     N = eng.mps.N
     seg = p.seg_len if p.seg_len else [N]
     halves = [build_half1(N, seg, 1, p.merge_turning), build_half1(N, seg, 2, p.merge_turning)]
+    nseg = len(seg)
     for _ in range(n_steps):
-        eng.gamma[0] = env_right(eng.gamma[1], eng._B(0), eng.W)
-        eng.beta[N - 1] = env_left(eng.beta[N - 2], eng._A(N - 2), eng.W)
+        if sweeps_right_first(0, nseg):
+            eng.gamma[0] = env_right(eng.gamma[1], eng._B(0), eng.W)
+        if not sweeps_right_first(nseg - 1, nseg):
+            eng.beta[N - 1] = env_left(eng.beta[N - 2], eng._A(N - 2), eng.W)
         for half in halves:
             for op in half:
                 run_op1(eng, op, p)

@@ -2735,9 +2735,17 @@ void step1_seg_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int
   const double tau = 0.5 * p->dt;
   tdvp_step_params pp = *p;  // boundary pairs: no weight cut beyond the relative cutoff
   pp.w_max = 0.0;
+  // the chain-end environment the first half reads first, rebuilt at the start
+  // of every step (a two-site half that ends moving away from that end leaves
+  // it behind): gamma_0 when segment 0 starts at site 0, beta_{N-1} when the
+  // last segment starts at site N-1 (segment k sweeps right first iff k and
+  // n_seg / 2 have the same parity)
+  const int ns = (int)seg.size();
+  const bool first_right = (0 % 2) == ((ns / 2) % 2);
+  const bool last_right = ((ns - 1) % 2) == ((ns / 2) % 2);
   for (int step = 0; step < n_steps; ++step) {
-    right_env(S, M, 0, s);      // gamma_0 and beta_{N-1} of the current state
-    left_env(S, M, N - 2, s);
+    if (first_right) right_env(S, M, 0, s);
+    if (!last_right) left_env(S, M, N - 2, s);
     for (int h = 0; h < 2; ++h) {
       const auto& ops = halves[h];
       size_t i = 0;
@@ -2791,12 +2799,9 @@ int tdvp_step_hybrid(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params,
     if (!mps || !mpo || !params) fail(TDVP_EINVAL, "NULL argument");
     if (n_steps < 0) fail(TDVP_EINVAL, "n_steps < 0");
     if (params->precision != TDVP_FP64) fail(TDVP_EINVAL, "the hybrid scheme is FP64 only");
-    tdvp_step_params serial = *params;  // the one-site sweep is serial
-    serial.n_seg = 0;
-    serial.seg_len = nullptr;
     for (int i = 0; i < n_steps; ++i) {
       if (bonds_saturated(mps, params->chi_max)) {
-        step1_impl(mps, mpo, &serial, 1, stats, (cudaStream_t)stream);
+        step1_impl(mps, mpo, params, 1, stats, (cudaStream_t)stream);
         ++n1;
       } else {
         step_impl(mps, mpo, params, 1, stats, (cudaStream_t)stream);

@@ -96,9 +96,9 @@ def _rank_main(rank, world, port, scheme, steps, out):
 
     for _ in range(steps):
         if scheme == 1:   # step1_segmented's rebuilds at the start of a step, by the owning ranks
-            if owner[0] == rank:
+            if owner[0] == rank and T.sweeps_right_first(0, len(SEG)):
                 eng.gamma[0] = T.env_right(eng.gamma[1], eng._B(0), W)
-            if owner[N - 1] == rank:
+            if owner[N - 1] == rank and not T.sweeps_right_first(len(SEG) - 1, len(SEG)):
                 eng.beta[N - 1] = T.env_left(eng.beta[N - 2], eng._A(N - 2), W)
         for ops, plan in zip(halves, plans):
             for stage in range(max(o.stage for o in ops) + 1):

@@ -54,7 +54,8 @@ def test_one_site_full_rank_is_exact():
     assert np.abs(tdvp.measure(mps, tdvp.OBS_SZ) - want).max() < 1e-9
 
 
-def test_hybrid_matches_oracle():
+@pytest.mark.parametrize("seg", [None, [4, 4]], ids=["serial", "segments"])
+def test_hybrid_matches_oracle(seg):
     torch_or_skip()
     tdvp = lib()
     N, chi = 8, 4
@@ -64,8 +65,8 @@ def test_hybrid_matches_oracle():
     up = I.basis_state("all_up", N)
     mps = tdvp.init_mps(N, up, chi)
     eng = T.Engine(M.product_state(up), W)
-    n1 = tdvp.step_hybrid(mps, mpo, tdvp.step_params(0.05, chi, krylov_max=24, krylov_tol=0.0), 12)
-    on1 = T1.step_hybrid(eng, T.Params(dt=0.05, chi_max=chi, krylov_max=24, krylov_tol=0.0), 12)
+    n1 = tdvp.step_hybrid(mps, mpo, tdvp.step_params(0.05, chi, krylov_max=24, krylov_tol=0.0, seg_len=seg), 12)
+    on1 = T1.step_hybrid(eng, T.Params(dt=0.05, chi_max=chi, krylov_max=24, krylov_tol=0.0, seg_len=seg), 12)
     assert n1 == on1 and 0 < n1 < 12
     assert list(mps.bond_dims()) == eng.mps.bond_dims()
     compare(tdvp, mps, mpo, eng, W, 1e-10)
