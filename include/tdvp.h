@@ -256,7 +256,8 @@ int tdvp_step(tdvp_mps mps, tdvp_mpo mpo, const tdvp_step_params* params, int n_
  * evolved together as in tdvp_step (Theta = Psi_e V_e Psi_{e+1}, V = Lambda^-1)
  * and split back at the bond's current dimension (cut only by eps), which
  * stands for their site terms and the bond term between them; per stage the
- * site steps and the boundary pairs of all segments run batched. Bond
+ * site steps, the bond steps and the boundary pairs of all segments each run
+ * batched. Bond
  * dimensions are kept; the boundary cuts change norm and energy by their
  * discarded weight. Exact at full bond dimension. The schedule is
  * tdvp_schedule1's. FP64 only. stats->n_back1 counts the site updates,

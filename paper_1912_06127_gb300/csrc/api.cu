@@ -2724,6 +2724,237 @@ void site_forward_batch(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<std::pai
 // batch, the boundary pairs as one batched two-site update at each bond's
 // current dimension, the bond steps one after another. Stages run in order;
 // the ops of a stage touch disjoint tensors, so their order does not matter.
+// One SVD split per item (rows[i] x cols[i] of theta[i], every value kept but
+// the numerical zeros), all problems in one batched launch sequence, each in
+// its own slot; returns the kept ranks.
+std::vector<int> device_split_batch(tdvp_mps_s* S, const std::vector<Slot*>& sl,
+                                    const std::vector<const double2*>& theta, const std::vector<int>& rows,
+                                    const std::vector<int>& cols, const std::vector<double2*>& PsiL,
+                                    const std::vector<double*>& V, const std::vector<double2*>& PsiR,
+                                    cudaStream_t s) {
+  const int n = (int)theta.size();
+  SvdBatch sb{};
+  sb.n = n;
+  sb.status = S->d_status;
+  sb.sync = sl[0]->sync;
+  for (int i = 0; i < n; ++i) {
+    SvdDesc& q = sb.d[i];
+    q = SvdDesc{};
+    q.theta = theta[i];
+    q.rows = rows[i];
+    q.cols = cols[i];
+    q.X = sl[i]->svdX;
+    q.Acc = sl[i]->svdAcc;
+    q.X32 = sl[i]->svdX32;
+    q.Acc32 = sl[i]->svdAcc32;
+    q.P = sl[i]->svdP;
+    q.T = sl[i]->svdT;
+    q.maxr = sl[i]->maxr;
+    q.sig = sl[i]->sig;
+    q.perm = sl[i]->perm;
+    q.rotated = sl[i]->rot;
+    q.conv = sl[i]->conv;
+    q.chi_max = std::min(rows[i], cols[i]);
+    q.w_max = 0.0;
+    q.eps = 0.0;
+    q.chi = S->d_chi + i;
+    q.w = S->d_w + i;
+    q.PsiL = PsiL[i];
+    q.V = V[i];
+    q.PsiR = PsiR[i];
+  }
+  svd_split(sb, S->d_flag, S->h_pinned, s);
+  read_stage_results(S, n, s);
+  std::vector<int> k(n);
+  for (int i = 0; i < n; ++i) k[i] = S->h_pinned[2 + i];
+  return k;
+}
+
+struct BondOp {
+  int kind;  // 1: bond j, the centre moving right (site j split, carried into j + 1);
+             // 2: bond j - 1, the centre moving left (site j split, carried into j - 1)
+  int j;
+  double t;  // evolution time of the bond matrix (negative: backward)
+};
+
+// The bond steps of one stage (bond_backward_right / _left), every phase
+// batched over the ops: split the site, build the environment of its
+// isometry, evolve the bond matrices with the zero-site term, split them,
+// carry them into the neighbour sites, rebuild the environments. The ops of a
+// stage belong to different segments and touch disjoint tensors.
+void bond_steps_batch(tdvp_mps_s* S, tdvp_mpo_s* M, const std::vector<BondOp>& ops, const tdvp_step_params* p,
+                      cudaStream_t s) {
+  const int n = (int)ops.size();
+  if (n == 0) return;
+  if (n > MAXB) fail(TDVP_EINVAL, "too many bond steps in a stage");
+  const int d = S->d, m = M->m;
+  const Ctx c64{s, S->d_status, TDVP_FP64};
+  std::vector<Slot*> sl(n);
+  for (int i = 0; i < n; ++i) sl[i] = slot_for(S, i, m, p->krylov_max);
+  std::vector<const double2*> th(n);
+  std::vector<int> rows(n), cols(n), A(n), B(n), a(n);
+  std::vector<double2*> P1(n), R1(n), P2(n), R2(n);
+  std::vector<double*> V1(n), V2(n);
+  for (int i = 0; i < n; ++i) {
+    const int j = ops[i].j;
+    P1[i] = sl[i]->theta;
+    R1[i] = sl[i]->theta2;
+    P2[i] = sl[i]->T1;
+    R2[i] = sl[i]->T2;
+    V1[i] = sl[i]->bv;
+    V2[i] = sl[i]->bv + sl[i]->cap_svd + 1;
+    th[i] = S->Psi[j];
+    if (ops[i].kind == 1) {
+      A[i] = S->chiL(j);
+      a[i] = S->dims[j];          // bond j
+      B[i] = S->chiR(j + 1);
+      rows[i] = A[i] * d;
+      cols[i] = a[i];
+    } else {
+      A[i] = S->chiL(j - 1);
+      a[i] = S->dims[j - 1];      // bond j - 1
+      B[i] = S->chiR(j);
+      rows[i] = a[i];
+      cols[i] = d * B[i];
+    }
+  }
+  // 1. split the site: P1 = U Lambda, V1 = 1 / Lambda, R1 = Lambda V^H
+  const std::vector<int> k = device_split_batch(S, sl, th, rows, cols, P1, V1, R1, s);
+  // 2. environment of the isometry: beta_{j+1} from U = P1 V1, or gamma_{j-1} from V1 R1
+  {
+    ScaleBatch scl{}, scr{};
+    std::vector<EnvProb> le, re;
+    for (int i = 0; i < n; ++i) {
+      const int j = ops[i].j;
+      if (ops[i].kind == 1) {
+        scl.d[scl.n++] = ScaleDesc{P1[i], sl[i]->Amat, V1[i], A[i], d, k[i], 0, nullptr, nullptr};
+        le.push_back(EnvProb{A[i], k[i], d, m, S->beta[j], sl[i]->Amat, S->beta[j + 1], M->w1.op(), sl[i]});
+      } else {
+        scr.d[scr.n++] = ScaleDesc{R1[i], sl[i]->Bmat, V1[i], k[i], d, B[i], 1, nullptr, nullptr};
+        re.push_back(EnvProb{k[i], B[i], d, m, S->gamma[j], sl[i]->Bmat, S->gamma[j - 1], M->w1t.op(), sl[i]});
+      }
+    }
+    launch_scale_bond(scl, s);
+    launch_scale_bond(scr, s);
+    env_batch(0, le, c64);
+    env_batch(1, re, c64);
+  }
+  // 3. the bond matrices (R1: k x a, or P1: a x k) evolved by the zero-site term
+  {
+    std::vector<MvProb> P(n);
+    std::vector<const double2*> x(n);
+    std::vector<double2*> y(n);
+    std::vector<double> t(n);
+    for (int i = 0; i < n; ++i) {
+      const int j = ops[i].j;
+      MvProb& q = P[i];
+      q = MvProb{};
+      q.D = 1;
+      q.m = m;
+      q.W = M->w0.op();
+      q.slot = sl[i];
+      if (ops[i].kind == 1) {
+        q.A = k[i];
+        q.B = a[i];
+        q.L = S->beta[j + 1];
+        q.R = S->gamma[j];
+        x[i] = y[i] = R1[i];
+      } else {
+        q.A = a[i];
+        q.B = k[i];
+        q.L = S->beta[j];
+        q.R = S->gamma[j - 1];
+        x[i] = y[i] = P1[i];
+      }
+      t[i] = ops[i].t;
+    }
+    expm_batch(P, x, y, t, p->krylov_max, p->krylov_tol, c64);
+  }
+  // 4. split them: P2 = u s, V2 = 1 / s, R2 = s v^H
+  std::vector<const double2*> cm(n);
+  std::vector<int> r2(n), c2(n);
+  for (int i = 0; i < n; ++i) {
+    cm[i] = ops[i].kind == 1 ? R1[i] : P1[i];
+    r2[i] = ops[i].kind == 1 ? k[i] : a[i];
+    c2[i] = ops[i].kind == 1 ? a[i] : k[i];
+  }
+  const std::vector<int> k2 = device_split_batch(S, sl, cm, r2, c2, P2, V2, R2, s);
+  // 5. carry the bond into the neighbour site and rebuild the split site
+  //    kind 1: Psi_{j+1} <- R2 V_j(old) Psi_{j+1} (via R1), Psi_j <- P1 V1 P2
+  //    kind 2: Psi_j <- R2 V1 R1, Psi_{j-1} <- Psi_{j-1} V_{j-1}(old) P2 (via P1)
+  std::vector<ZGemmDesc> gs;
+  auto gemm = [](int Mm, int Nn, int Kk, const double2* Am, int64_t lda, const double* ks, const double2* Bm,
+                 int64_t ldb, double2* Cm, int64_t ldc) {
+    ZGemmDesc z{};
+    z.M = Mm;
+    z.N = Nn;
+    z.K = Kk;
+    z.A = Am;
+    z.a_rs = lda;
+    z.a_cs = 1;
+    z.kscale = ks;
+    z.B = Bm;
+    z.b_rs = ldb;
+    z.b_cs = 1;
+    z.C = Cm;
+    z.c_rs = ldc;
+    z.c_cs = 1;
+    return z;
+  };
+  for (int i = 0; i < n; ++i) {
+    const int j = ops[i].j;
+    if (ops[i].kind == 1) {
+      gs.push_back(gemm(k2[i], d * B[i], a[i], R2[i], a[i], S->V[j], S->Psi[j + 1], (int64_t)d * B[i], R1[i],
+                        (int64_t)d * B[i]));
+      gs.push_back(gemm(A[i] * d, k2[i], k[i], P1[i], k[i], V1[i], P2[i], k2[i], S->Psi[j], k2[i]));
+    } else {
+      gs.push_back(gemm(k2[i], d * B[i], k[i], R2[i], k[i], V1[i], R1[i], (int64_t)d * B[i], S->Psi[j],
+                        (int64_t)d * B[i]));
+      gs.push_back(gemm(A[i] * d, k2[i], a[i], S->Psi[j - 1], a[i], S->V[j - 1], P2[i], k2[i], P1[i], k2[i]));
+    }
+  }
+  for (size_t b0 = 0; b0 < gs.size(); b0 += MAXB) {
+    ZGemmBatch g{};
+    for (size_t q = b0; q < gs.size() && g.n < MAXB; ++q) g.d[g.n++] = gs[q];
+    launch_zgemm(g, s, "one_site_zgemm");
+  }
+  for (int i = 0; i < n; ++i) {
+    const int j = ops[i].j;
+    if (ops[i].kind == 1) {
+      CUDA_TRY(cudaMemcpyAsync(S->Psi[j + 1], R1[i], sizeof(double2) * k2[i] * d * B[i], cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(S->V[j], V2[i], sizeof(double) * k2[i], cudaMemcpyDeviceToDevice, s));
+      S->dims[j] = k2[i];
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(S->Psi[j - 1], P1[i], sizeof(double2) * A[i] * d * k2[i], cudaMemcpyDeviceToDevice,
+                               s));
+      CUDA_TRY(cudaMemcpyAsync(S->V[j - 1], V2[i], sizeof(double) * k2[i], cudaMemcpyDeviceToDevice, s));
+      S->dims[j - 1] = k2[i];
+    }
+  }
+  // 6. environments of the new gauge: beta_{j+1} from Psi_j V_j, or gamma_{j-1} from V_{j-1} Psi_j
+  {
+    ScaleBatch scl{}, scr{};
+    std::vector<EnvProb> le, re;
+    for (int i = 0; i < n; ++i) {
+      const int j = ops[i].j;
+      if (ops[i].kind == 1) {
+        scl.d[scl.n++] = ScaleDesc{S->Psi[j], sl[i]->Amat, S->V[j], S->chiL(j), d, S->chiR(j), 0, nullptr, nullptr};
+        le.push_back(EnvProb{S->chiL(j), S->chiR(j), d, m, S->beta[j], sl[i]->Amat, S->beta[j + 1], M->w1.op(),
+                             sl[i]});
+      } else {
+        scr.d[scr.n++] = ScaleDesc{S->Psi[j], sl[i]->Bmat, S->V[j - 1], S->chiL(j), d, S->chiR(j), 1, nullptr,
+                                   nullptr};
+        re.push_back(EnvProb{S->chiL(j), S->chiR(j), d, m, S->gamma[j], sl[i]->Bmat, S->gamma[j - 1], M->w1t.op(),
+                             sl[i]});
+      }
+    }
+    launch_scale_bond(scl, s);
+    launch_scale_bond(scr, s);
+    env_batch(0, le, c64);
+    env_batch(1, re, c64);
+  }
+}
+
 void step1_seg_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int n_steps, tdvp_step_stats* st,
                     cudaStream_t s) {
   const int N = S->N;
@@ -2761,9 +2992,10 @@ void step1_seg_impl(tdvp_mps_s* S, tdvp_mpo_s* M, const tdvp_step_params* p, int
           else bonds.push_back(&o);
         }
         site_forward_batch(S, M, sites, p, st, s);
-        for (const SchedOp* o : bonds) {
-          if (o->kind == 1) bond_backward_right(S, M, o->j, o->tfac * tau, p, s);
-          else bond_backward_left(S, M, o->j, o->tfac * tau, p, s);
+        {
+          std::vector<BondOp> bops;
+          for (const SchedOp* o : bonds) bops.push_back(BondOp{o->kind, o->j, -o->tfac * tau});
+          bond_steps_batch(S, M, bops, p, s);
         }
         if (!pairs.empty()) run_fwd2(S, M, pairs, &pp, st, s);
         if (st) st->n_stages += 1;

@@ -58,6 +58,7 @@ struct Slot {
   int* perm = nullptr;
   int* rot = nullptr;
   int* conv = nullptr;
+  double* bv = nullptr;       // two bond vectors of cap_svd values (one-site bond steps)
   void ensure(int64_t vec, int64_t T, int64_t fsz, int64_t svd_n, int kmax_);
   void release();
   ~Slot() { release(); }

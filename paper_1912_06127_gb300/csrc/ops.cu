@@ -195,14 +195,16 @@ void Slot::ensure(int64_t vec, int64_t T, int64_t fsz, int64_t svd_n, int kmax_)
   perm = dalloc<int>(nsvd + 1);
   rot = dalloc<int>(2);  // rotations, pairs checked
   conv = dalloc<int>(1);
+  bv = dalloc<double>(2 * (nsvd + 1));
 }
 
 void Slot::release() {
   for (void* p : {(void*)theta, (void*)theta2, (void*)V, (void*)T1, (void*)T2, (void*)Amat, (void*)Bmat,
                   (void*)st, (void*)part, (void*)counter, (void*)svdX, (void*)svdAcc, (void*)sig,
                   (void*)perm, (void*)rot, (void*)conv, (void*)svdP, (void*)svdT, (void*)svdX32,
-                  (void*)svdAcc32, (void*)maxr, (void*)sync})
+                  (void*)svdAcc32, (void*)maxr, (void*)sync, (void*)bv})
     dfree(p);
+  bv = nullptr;
   for (auto& p : f) {
     dfree(p);
     p = nullptr;
