@@ -674,11 +674,14 @@ __device__ inline bool jacobi_rotation_fast(typename Prec<T>::R tol2, typename P
   return true;
 }
 
+// x' = cs x + m1 y, y' = cs y + m2 x with m2 = (-re m1, im m1) (the rotation
+// is unitary: m2 = -conj(m1)), so only cs and m1 are read
 template <typename T>
 __device__ inline void apply_rot(T& u, T& v, const RotRec<T>& r) {
   const T x = u, y = v;
-  u = Prec<T>::mk(r.cs * x.x + r.m1.x * y.x - r.m1.y * y.y, r.cs * x.y + r.m1.x * y.y + r.m1.y * y.x);
-  v = Prec<T>::mk(r.cs * y.x + r.m2.x * x.x - r.m2.y * x.y, r.cs * y.y + r.m2.x * x.y + r.m2.y * x.x);
+  const auto m1x = r.m1.x, m1y = r.m1.y, m2x = -r.m1.x;
+  u = Prec<T>::mk(r.cs * x.x + m1x * y.x - m1y * y.y, r.cs * x.y + m1x * y.y + m1y * y.x);
+  v = Prec<T>::mk(r.cs * y.x + m2x * x.x - m1y * x.y, r.cs * y.y + m2x * x.y + m1y * x.x);
 }
 
 // Cross product <x, y> of two vectors in shared memory, summed over the warp.
@@ -846,8 +849,6 @@ __device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec
       rec.cs = __shfl_sync(0xffffffffu, rec.cs, 0);
       rec.m1.x = __shfl_sync(0xffffffffu, rec.m1.x, 0);
       rec.m1.y = __shfl_sync(0xffffffffu, rec.m1.y, 0);
-      rec.m2.x = __shfl_sync(0xffffffffu, rec.m2.x, 0);
-      rec.m2.y = __shfl_sync(0xffffffffu, rec.m2.y, 0);
 #pragma unroll
       for (int i = 0; i < C::EPT; ++i) {
         T u = x[lane + 32 * i], v = y[lane + 32 * i];
