@@ -113,6 +113,8 @@ __device__ inline float warp_sumf(float v) {
   return v;
 }
 
+constexpr int GV = 32;  // vectors of a visit in the Gram form of the FP32 phase (below)
+
 // Element types of the Jacobi sweeps: double2 (complex FP64), float2 (complex
 // FP32) and float4 (complex double-float: re_hi, im_hi, re_lo, im_lo; value =
 // hi + lo, ~48 significant bits, computed on the FP32 pipe). R: Gram entries,
@@ -509,10 +511,11 @@ __device__ inline void sweep_end(const SvdBatch& B, float stop, double* work_flo
   for (int i = 0; i < B.n; ++i) {
     const SvdDesc& P = B.d[i];
     if (!*P.conv) {
-      // arithmetic of this sweep in the phase's precision: the cross product
-      // <x, y> of every pair checked (8 flops per element), the rotation of
-      // the vectors (20 per element) and, when it runs in this precision, of
-      // the rows of Acc
+      // arithmetic of this sweep in the phase's precision, counted as in the
+      // rotation form: the cross product <x, y> of every pair checked (8 flops
+      // per element), the rotation of the vectors (20 per element) and, when it
+      // runs in this precision, of the rows of Acc (the Gram form of the FP32
+      // phase does the same work as dense block products)
       if (work_flops) {
         const double per_rot = 20.0 * P.len + (acc_in_phase ? 20.0 * P.n_vec : 0.0);
         work_flops[0] += 8.0 * P.len * (double)P.rotated[1] + per_rot * (double)P.rotated[0];
@@ -615,15 +618,6 @@ struct RotRec {
   float2 m1l, m2l;
 };
 
-template <typename T, int W>
-constexpr size_t block_smem_bytes() {
-  using C = BlockCfg<T, W>;
-  using R = typename Prec<T>::R;
-  size_t b = (size_t)2 * W * C::LMAX * sizeof(T);       // the vectors
-  b += (size_t)C::MAX_STEPS * W * sizeof(RotRec<T>);    // rotation record
-  b += (size_t)2 * W * sizeof(R);                       // squared norms
-  return b;
-}
 
 // Round-robin pairing of n_even items: pair `k` of round `r` (0 <= r < n_even - 1).
 __host__ __device__ constexpr void rr_pair(int n_even, int r, int k, int& p, int& q) {
@@ -999,6 +993,349 @@ __device__ inline void block_correct_acc(const SvdDesc& P, const int* vrows, con
   }
 }
 
+// ---------------------------------------------------------------------------
+// Gram form of a visit (the FP32 phase). The rotations of a visit need only
+// the norms and cross products of its 2W vectors, i.e. the Hermitian Gram
+// matrix G = X^H X of the block pair (G[a][b] = <x_a, x_b>). It is formed once
+// per visit, in one pass over the vectors; the rotations -- the same pairs in
+// the same order as in the rotation form above -- are found from G and applied
+// to G (G <- J^H G J, a 2 x 2 block of pairs per thread) and to the visit's
+// rotation Q (Q <- Q J, from the identity); the vectors and the rows of Acc
+// are then updated once, x_j <- sum_k Q[k][j] x_k, by register-tiled products.
+// The work per pair that grows with the vector length (a cross product and a
+// rotation of two vectors, a rotation of two rows of Acc) becomes three dense
+// products per visit, and only O(W) work per pair stays in the chain of
+// dependent rotations. In exact arithmetic this is the rotation form's visit;
+// in FP32, G is updated rather than recomputed between the rotations, which
+// changes them at the level of FP32 rounding -- the phase is a preconditioner
+// whose rotation is made unitary and whose vectors are recomputed in FP64
+// afterwards. W = 16: 32 vectors, 512 threads.
+// ---------------------------------------------------------------------------
+
+struct GramRot {
+  float cs;
+  float2 m1, m2;
+  int rot;
+};
+
+constexpr int GSTEPS = GV - 1;  // local rounds: W - 1 inside the blocks, W across them
+
+struct __align__(16) GramShared {
+  float2 G[GV][GV];
+  float2 Q[GV][GV];
+  GramRot rr[GV / 2];                    // the rotations of the current local round
+  unsigned char pq[GSTEPS][GV / 2][2];   // the pairs (p < q) of each local round
+  unsigned char tile[36][2];  // the 4 x 4 tiles (ti <= tj) of G formed by the warps
+  unsigned char blk[120][2];  // the pairs of pairs (u < v) whose 2 x 2 blocks the rotations update
+  int vrows[GV];
+  int n_rot;
+};
+
+// Pair w of local round rr: the pairs inside each of the two blocks (intra) or
+// across them, as in the rotation form.
+template <int W>
+__device__ inline void gram_pair(bool intra, int rr, int w, int& p, int& q) {
+  if (intra) {
+    rr_pair(W, rr, w % (W / 2), p, q);
+    if (w >= W / 2) {
+      p += W;
+      q += W;
+    }
+  } else {
+    p = w;
+    q = W + (w + rr) % W;
+  }
+}
+
+// Sums v[0 .. 31] over the lanes of a warp by recursive halving; lane l returns
+// the total of v[l].
+__device__ inline float warp_reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? v[i] : v[i + h];
+      const float keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  return v[0];
+}
+
+__device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ inline float2 cmulc(float2 a, float2 b) {  // conj(a) b
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ inline float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ inline float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// out_j = sum_k Q[k][j] in_k for the GV rows of `rows` (ncols <= 512 columns,
+// row stride 512), written to dst[vrows[j] * stride + c] for the present rows.
+// A thread holds 4 rows x 4 columns of the result (columns c, c + 64, c + 128,
+// c + 192 of a half of 256 columns); the halves are done one after the other.
+// `between` runs after the last read of `rows` (all threads have passed a
+// barrier), before the second half's results are stored.
+template <typename F>
+__device__ inline void gram_apply_q(const float2* rows, const GramShared& S, int ncols, float2* dst, int stride,
+                                    F&& between) {
+  constexpr int LMAX = 512;
+  const int tid = threadIdx.x;
+  const int cg = tid & 63, rg = tid >> 6;
+  for (int half = 0; half < 2; ++half) {
+    const int c0 = 256 * half + cg;
+    const int nu = ncols > c0 ? min(4, (ncols - c0 + 63) >> 6) : 0;
+    float2 acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[j][u] = make_float2(0.f, 0.f);
+    if (256 * half < ncols) {
+#pragma unroll 4
+      for (int k = 0; k < GV; ++k) {
+        float2 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = rows[k * LMAX + c0 + 64 * u];
+        const float4* qk = reinterpret_cast<const float4*>(&S.Q[k][4 * rg]);
+        const float4 q01 = qk[0], q23 = qk[1];
+        const float2 q[4] = {make_float2(q01.x, q01.y), make_float2(q01.z, q01.w), make_float2(q23.x, q23.y),
+                             make_float2(q23.z, q23.w)};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            acc[j][u].x += q[j].x * x[u].x - q[j].y * x[u].y;
+            acc[j][u].y += q[j].x * x[u].y + q[j].y * x[u].x;
+          }
+      }
+    }
+    if (half == 1) {
+      __syncthreads();  // every thread is done reading `rows`
+      between();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = S.vrows[4 * rg + j];
+      if (r < 0) continue;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u < nu) dst[(int64_t)r * stride + c0 + 64 * u] = acc[j][u];
+    }
+  }
+}
+
+// Loads the GV rows `vrows` of src (row stride `stride`, `ncols` columns) into
+// `rows` (row stride 512), zero for columns in [ncols, ncols_pad) and for
+// absent rows; 16-byte asynchronous copies (cp.async, zero-filled where there
+// is no source) when ncols and stride are even, else plain loads. Ends with
+// the copies complete and a barrier.
+__device__ inline void gram_load_rows(float2* rows, const float2* src, const int* vrows, int ncols, int ncols_pad,
+                                      int stride) {
+  constexpr int LMAX = 512;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (((ncols | stride) & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    const int nch = (ncols_pad + 1) >> 1;  // 16-byte chunks per row
+    for (int i = tid; i < GV * nch; i += nthr) {
+      const int k = i / nch, ch = i - k * nch;
+      const int r = vrows[k];
+      const bool have = r >= 0 && 2 * ch < ncols;
+      const float2* g = have ? src + (int64_t)r * stride + 2 * ch : src;
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(rows + k * LMAX + 2 * ch);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(g), "r"(have ? 16 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  } else {
+    for (int i = tid; i < GV * ncols_pad; i += nthr) {
+      const int k = i / ncols_pad, e = i - k * ncols_pad;
+      const int r = vrows[k];
+      rows[k * LMAX + e] = (r >= 0 && e < ncols) ? src[(int64_t)r * stride + e] : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+}
+
+// The tables of the Gram form (once per kernel).
+template <int W>
+__device__ inline void gram_tables(GramShared& S) {
+  const int tid = threadIdx.x;
+  if (tid < GSTEPS * (GV / 2)) {
+    const int st = tid / (GV / 2), w = tid % (GV / 2);
+    int p, q;
+    gram_pair<W>(st < W - 1, st < W - 1 ? st : st - (W - 1), w, p, q);
+    S.pq[st][w][0] = (unsigned char)p;
+    S.pq[st][w][1] = (unsigned char)q;
+  }
+  if (tid < 36) {
+    int t = tid, ti = 0;
+    while (t >= 8 - ti) t -= 8 - ti++;
+    S.tile[tid][0] = (unsigned char)ti;
+    S.tile[tid][1] = (unsigned char)(ti + t);
+  }
+  if (tid < 120) {
+    int t = tid, u = 0;
+    while (t >= 15 - u) t -= 15 - u++;
+    S.blk[tid][0] = (unsigned char)u;
+    S.blk[tid][1] = (unsigned char)(u + 1 + t);
+  }
+}
+
+// One visit in the Gram form: blocks bi and bj (bj may be the padding block).
+template <int W>
+__device__ void block_visit_gram(const SvdDesc& P, int bi, int bj, bool first_round, float tol, float2* xs,
+                                 GramShared& S) {
+  static_assert(2 * W == GV, "Gram form: blocks of 16");
+  constexpr int THREADS = 32 * W;
+  constexpr int LMAX = 512;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = P.n_vec, len = P.len;
+  const int nb = (n + W - 1) / W;
+  __syncthreads();  // the previous visit is done with S and xs
+  if (tid < GV) {
+    const int blk = tid < W ? bi : bj;
+    const int g = blk * W + (tid % W);
+    S.vrows[tid] = (blk < nb && g < n) ? g : -1;
+  }
+  __syncthreads();
+  const bool j_real = bj < nb;
+  if (!first_round && !j_real) return;
+  // Q = I; the vectors (zero up to a multiple of 32 elements and for absent vectors)
+  float2* X = P.X32;
+  const int nst = (len + 31) >> 5;
+  for (int i = tid; i < GV * GV; i += THREADS) (&S.Q[0][0])[i] = make_float2(i / GV == i % GV ? 1.f : 0.f, 0.f);
+  gram_load_rows(xs, X, S.vrows, len, 32 * nst, len);
+  // G: the upper 4 x 4 tiles, a warp per tile, the lanes splitting the elements
+  for (int t = warp; t < 36; t += W) {
+    const int ti = S.tile[t][0], tj = S.tile[t][1];
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+    const float2* xa = xs + 4 * ti * LMAX + lane;
+    const float2* xb = xs + 4 * tj * LMAX + lane;
+    for (int s = 0; s < nst; ++s) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = xa[i * LMAX + 32 * s];
+        b[i] = xb[i * LMAX + 32 * s];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[2 * (4 * i + j)] += a[i].x * b[j].x + a[i].y * b[j].y;
+          acc[2 * (4 * i + j) + 1] += a[i].x * b[j].y - a[i].y * b[j].x;
+        }
+    }
+    const float v = warp_reduce_scatter32(acc, lane);
+    const int e = lane >> 1, i = e >> 2, j = e & 3, c = lane & 1;
+    float* Gf = reinterpret_cast<float*>(&S.G[0][0]);
+    Gf[((4 * ti + i) * GV + 4 * tj + j) * 2 + c] = v;
+    if (ti != tj) Gf[((4 * tj + j) * GV + 4 * ti + i) * 2 + c] = c ? -v : v;
+  }
+  __syncthreads();
+  // the rotations, in local rounds of W disjoint pairs: steps 0 .. W - 2 pair
+  // the vectors inside each block, steps W - 1 .. 2W - 2 across the blocks
+  const float zl = Prec<float2>::zero_level(P);
+  const float tol2 = tol * tol;
+  int lrot = 0, lchk = 0;
+  float lmax = 0.f;
+  const int st0 = first_round ? 0 : W - 1;
+  const int st1 = j_real ? 2 * W - 2 : W - 2;  // last step
+  for (int st = st0; st <= st1; ++st) {
+    if (tid < W) {
+      // the parameters of pair tid (one lane per pair), from G
+      const int p = S.pq[st][tid][0], q = S.pq[st][tid][1];
+      GramRot g{1.f, make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0};
+      if (S.vrows[p] >= 0 && S.vrows[q] >= 0) {
+        ++lchk;
+        const float a = S.G[p][p].x, b = S.G[q][q].x;
+        const float2 k = S.G[p][q];
+        RotRec<float2> rec;
+        float a2, b2, ratio = 0.f;
+        if (jacobi_rotation_fast<float2>(tol2, zl, a, b, k.x, k.y, rec, a2, b2, ratio)) {
+          g = GramRot{rec.cs, rec.m1, rec.m2, 1};
+          ++lrot;
+          lmax = fmaxf(lmax, ratio);
+          S.G[p][p] = make_float2(a2, 0.f);
+          S.G[q][q] = make_float2(b2, 0.f);
+          S.G[p][q] = S.G[q][p] = make_float2(0.f, 0.f);
+        }
+      }
+      S.rr[tid] = g;
+    }
+    __syncthreads();
+    {
+      // Q <- Q J: row k, pair w (x_p' = cs x_p + m1 x_q, x_q' = m2 x_p + cs x_q)
+      const int k = tid >> 4, w = tid & 15;
+      const GramRot& g = S.rr[w];
+      if (g.rot) {
+        const int p = S.pq[st][w][0], q = S.pq[st][w][1];
+        const float2 a = S.Q[k][p], b = S.Q[k][q];
+        S.Q[k][p] = cadd(cscale(g.cs, a), cmul(g.m1, b));
+        S.Q[k][q] = cadd(cmul(g.m2, a), cscale(g.cs, b));
+      }
+    }
+    if (tid >= THREADS - 120) {
+      // G <- J^H G J on the 2 x 2 block (pair u) x (pair v), u < v, and its mirror
+      const int t = tid - (THREADS - 120);
+      const int u = S.blk[t][0], v = S.blk[t][1];
+      const GramRot gu = S.rr[u], gv = S.rr[v];
+      if (gu.rot | gv.rot) {
+        const int p = S.pq[st][u][0], q = S.pq[st][u][1];
+        const int r = S.pq[st][v][0], s = S.pq[st][v][1];
+        const float2 g_pr = S.G[p][r], g_ps = S.G[p][s], g_qr = S.G[q][r], g_qs = S.G[q][s];
+        // columns: (G J_v)[., r] = G[., r] cs + G[., s] m1; (G J_v)[., s] = G[., r] m2 + G[., s] cs
+        const float2 t_pr = cadd(cscale(gv.cs, g_pr), cmul(g_ps, gv.m1));
+        const float2 t_ps = cadd(cmul(g_pr, gv.m2), cscale(gv.cs, g_ps));
+        const float2 t_qr = cadd(cscale(gv.cs, g_qr), cmul(g_qs, gv.m1));
+        const float2 t_qs = cadd(cmul(g_qr, gv.m2), cscale(gv.cs, g_qs));
+        // rows: (J_u^H T)[p, .] = cs T[p, .] + conj(m1) T[q, .]; [q, .] = conj(m2) T[p, .] + cs T[q, .]
+        const float2 n_pr = cadd(cscale(gu.cs, t_pr), cmulc(gu.m1, t_qr));
+        const float2 n_ps = cadd(cscale(gu.cs, t_ps), cmulc(gu.m1, t_qs));
+        const float2 n_qr = cadd(cmulc(gu.m2, t_pr), cscale(gu.cs, t_qr));
+        const float2 n_qs = cadd(cmulc(gu.m2, t_ps), cscale(gu.cs, t_qs));
+        S.G[p][r] = n_pr;
+        S.G[p][s] = n_ps;
+        S.G[q][r] = n_qr;
+        S.G[q][s] = n_qs;
+        S.G[r][p] = conjf2(n_pr);
+        S.G[s][p] = conjf2(n_ps);
+        S.G[r][q] = conjf2(n_qr);
+        S.G[s][q] = conjf2(n_qs);
+      }
+    }
+    __syncthreads();
+  }
+  if (warp == 0) {
+    int nr = lrot, nc = lchk;
+    float m = lmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nr += __shfl_xor_sync(0xffffffffu, nr, o);
+      nc += __shfl_xor_sync(0xffffffffu, nc, o);
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) {
+      S.n_rot = nr;
+      if (nc > 0) atomicAdd(P.rotated + 1, nc);
+      if (nr > 0) {
+        atomicAdd(P.rotated, nr);
+        atomicMax(P.maxr, __float_as_uint(m));
+      }
+    }
+  }
+  __syncthreads();
+  if (S.n_rot == 0) return;  // the vectors are unchanged
+  // X <- X Q; once xs has been read, the rows of Acc are copied into it while
+  // the last results of X Q are stored
+  float2* A = P.Acc32;
+  gram_apply_q(xs, S, len, X, len, [&] { gram_load_rows(xs, A, S.vrows, n, n, n); });
+  gram_apply_q(xs, S, n, A, n, [] {});
+}
+
 // One visit: blocks bi and bj (bj may be the padding block) of problem P.
 // acc_mode 0: replay every rotation on Acc; 1: block_correct_acc (FP64 sweeps
 // of the mixed mode).
@@ -1100,7 +1437,19 @@ __device__ void block_visit(const SvdDesc& P, int bi, int bj, bool first_round, 
   }
 }
 
+template <typename T, int W>
+constexpr size_t block_smem_bytes() {
+  using C = BlockCfg<T, W>;
+  using R = typename Prec<T>::R;
+  size_t b = (size_t)2 * W * C::LMAX * sizeof(T);       // the vectors
+  if (std::is_same<T, float2>::value) return b + sizeof(GramShared);  // the Gram form's state
+  b += (size_t)C::MAX_STEPS * W * sizeof(RotRec<T>);    // rotation record
+  b += (size_t)2 * W * sizeof(R);                       // squared norms
+  return b;
+}
+
 // All sweeps of one phase with the block order (see above); one CTA per SM.
+// The FP32 phase (T = float2) runs its visits in the Gram form.
 template <typename T, int W, int MINB>
 __global__ void __launch_bounds__(32 * W, MINB) svd_block_sweeps(const __grid_constant__ SvdBatch B, int nbpad_max,
                                                                 float stop, double tol, int max_sweeps, int fatal,
@@ -1111,6 +1460,8 @@ __global__ void __launch_bounds__(32 * W, MINB) svd_block_sweeps(const __grid_co
   T* xs = reinterpret_cast<T*>(smem_raw);
   RotRec<T>* seq = reinterpret_cast<RotRec<T>*>(smem_raw + (size_t)2 * W * C::LMAX * sizeof(T));
   R* nrm = reinterpret_cast<R*>(seq + C::MAX_STEPS * W);
+  GramShared* gs = reinterpret_cast<GramShared*>(smem_raw + (size_t)2 * W * C::LMAX * sizeof(T));
+  if constexpr (std::is_same<T, float2>::value) gram_tables<W>(*gs);
   __shared__ int off[MAXB + 1];
   if (threadIdx.x == 0) {
     off[0] = 0;
@@ -1148,7 +1499,10 @@ __global__ void __launch_bounds__(32 * W, MINB) svd_block_sweeps(const __grid_co
         if (br >= nbp - 1) continue;
         int bi, bj;
         rr_pair(nbp, br, u - off[pid], bi, bj);
-        block_visit<T, W>(P, bi, bj, br == 0, use_order != 0, acc_mode, (R)tol, xs, seq, nrm);
+        if constexpr (std::is_same<T, float2>::value)
+          block_visit_gram<W>(P, bi, bj, br == 0, (float)tol, xs, *gs);
+        else
+          block_visit<T, W>(P, bi, bj, br == 0, use_order != 0, acc_mode, (R)tol, xs, seq, nrm);
       }
       if (!grid_barrier(B.sync, gridDim.x, B.status, B.spin_limit)) return;
     }
