@@ -111,6 +111,55 @@ __device__ inline void dd_acc(float& s, float& c, float ah, float al, float bh, 
   two_sum(s, p, s, t);
   c += t + fmaf(ah, bl, fmaf(al, bh, e));
 }
+// ---- packed FP32 pairs (sm_100 and later: the .f32x2 forms of add, sub, mul
+// and fma, two lanes per instruction, each lane rounded as its scalar form) ----
+// A pair is a 64-bit register with its first element in the low half, as a
+// float2 in memory.
+typedef unsigned long long f32x2;
+__device__ inline f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ inline float2 upk2(f32x2 v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return make_float2(lo, hi);
+}
+__device__ inline f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ inline f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ inline f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ inline f32x2 fma2r(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ inline void fma2(f32x2& acc, f32x2 a, f32x2 b) { acc = fma2r(a, b, acc); }
+// dd_acc on both lanes of the pairs (s, c) with the same operations in the
+// same order as the scalar form, so each lane's result is bitwise the scalar
+// one: nah = -ah (exact), so np = (-ah) bh = -p exactly, e = fma(ah, bh, np),
+// s + p = s - np and p - bb = -(np + bb).
+__device__ inline void dd_acc2(f32x2& s, f32x2& c, f32x2 ah, f32x2 nah, f32x2 al, f32x2 bh, f32x2 bl) {
+  const f32x2 np = mul2(nah, bh);
+  const f32x2 e = fma2r(ah, bh, np);
+  const f32x2 s1 = sub2(s, np);
+  const f32x2 bb = sub2(s1, s);
+  const f32x2 t = sub2(sub2(s, sub2(s1, bb)), add2(np, bb));
+  s = s1;
+  c = add2(c, add2(t, fma2r(ah, bl, fma2r(al, bh, e))));
+}
 // double -> (hi, lo) floats
 __device__ inline float2 dd_split(double x) {
   const float h = (float)x;

@@ -1023,6 +1023,7 @@ constexpr int GSTEPS = GV - 1;  // local rounds: W - 1 inside the blocks, W acro
 struct __align__(16) GramShared {
   float2 G[GV][GV];
   float2 Q[GV][GV];
+  float2 QS[GV][GV];                     // i Q = (-im Q, re Q), for the packed products
   GramRot rr[GV / 2];                    // the rotations of the current local round
   unsigned char pq[GSTEPS][GV / 2][2];   // the pairs (p < q) of each local round
   unsigned char tile[36][2];  // the 4 x 4 tiles (ti <= tj) of G formed by the warps
@@ -1071,10 +1072,19 @@ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x
 __device__ inline float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
 __device__ inline float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
+
 // out_j = sum_k Q[k][j] in_k for the GV rows of `rows` (ncols <= 512 columns,
 // row stride 512), written to dst[vrows[j] * stride + c] for the present rows.
 // A thread holds 4 rows x 4 columns of the result (columns c, c + 64, c + 128,
 // c + 192 of a half of 256 columns); the halves are done one after the other.
+// `between` runs after the last read of `rows` (all threads have passed a
+// barrier), before the second half's results are stored.
+// out_j = sum_k Q[k][j] in_k for the GV rows of `rows` (ncols <= 512 columns,
+// row stride 512), written to dst[vrows[j] * stride + c] for the present rows.
+// A thread holds 4 rows x 4 columns of the result (columns c, c + 64, c + 128,
+// c + 192 of a half of 256 columns); the halves are done one after the other.
+// A complex multiply-add is two packed FMAs: out += (re x, re x) (re q, im q)
+// + (im x, im x) (-im q, re q), the second factors read from Q and QS.
 // `between` runs after the last read of `rows` (all threads have passed a
 // barrier), before the second half's results are stored.
 template <typename F>
@@ -1086,28 +1096,30 @@ __device__ inline void gram_apply_q(const float2* rows, const GramShared& S, int
   for (int half = 0; half < 2; ++half) {
     const int c0 = 256 * half + cg;
     const int nu = ncols > c0 ? min(4, (ncols - c0 + 63) >> 6) : 0;
-    float2 acc[4][4];
+    f32x2 acc[4][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[j][u] = make_float2(0.f, 0.f);
+      for (int u = 0; u < 4; ++u) acc[j][u] = 0ull;
     if (256 * half < ncols) {
 #pragma unroll 4
       for (int k = 0; k < GV; ++k) {
         float2 x[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) x[u] = rows[k * LMAX + c0 + 64 * u];
-        const float4* qk = reinterpret_cast<const float4*>(&S.Q[k][4 * rg]);
-        const float4 q01 = qk[0], q23 = qk[1];
-        const float2 q[4] = {make_float2(q01.x, q01.y), make_float2(q01.z, q01.w), make_float2(q23.x, q23.y),
-                             make_float2(q23.z, q23.w)};
+        const ulonglong2* qk = reinterpret_cast<const ulonglong2*>(&S.Q[k][4 * rg]);
+        const ulonglong2* sk = reinterpret_cast<const ulonglong2*>(&S.QS[k][4 * rg]);
+        const ulonglong2 q01 = qk[0], q23 = qk[1], s01 = sk[0], s23 = sk[1];
+        const f32x2 q[4] = {q01.x, q01.y, q23.x, q23.y}, qs[4] = {s01.x, s01.y, s23.x, s23.y};
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int u = 0; u < 4; ++u) {
+          const f32x2 xr = pk2(x[u].x, x[u].x), xi = pk2(x[u].y, x[u].y);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            acc[j][u].x += q[j].x * x[u].x - q[j].y * x[u].y;
-            acc[j][u].y += q[j].x * x[u].y + q[j].y * x[u].x;
+          for (int j = 0; j < 4; ++j) {
+            fma2(acc[j][u], xr, q[j]);
+            fma2(acc[j][u], xi, qs[j]);
           }
+        }
       }
     }
     if (half == 1) {
@@ -1120,7 +1132,7 @@ __device__ inline void gram_apply_q(const float2* rows, const GramShared& S, int
       if (r < 0) continue;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (u < nu) dst[(int64_t)r * stride + c0 + 64 * u] = acc[j][u];
+        if (u < nu) dst[(int64_t)r * stride + c0 + 64 * u] = upk2(acc[j][u]);
     }
   }
 }
@@ -1209,9 +1221,10 @@ __device__ void block_visit_gram(const SvdDesc& P, int bi, int bj, bool first_ro
   // G: the upper 4 x 4 tiles, a warp per tile, the lanes splitting the elements
   for (int t = warp; t < 36; t += W) {
     const int ti = S.tile[t][0], tj = S.tile[t][1];
-    float acc[32];
+    // conj(a) b = (re a, re a) (re b, im b) + (im a, im a) (im b, -re b), packed
+    f32x2 acc2[16];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+    for (int i = 0; i < 16; ++i) acc2[i] = 0ull;
     const float2* xa = xs + 4 * ti * LMAX + lane;
     const float2* xb = xs + 4 * tj * LMAX + lane;
     for (int s = 0; s < nst; ++s) {
@@ -1221,13 +1234,28 @@ __device__ void block_visit_gram(const SvdDesc& P, int bi, int bj, bool first_ro
         a[i] = xa[i * LMAX + 32 * s];
         b[i] = xb[i * LMAX + 32 * s];
       }
+      f32x2 bv[4], bs[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        bv[j] = pk2(b[j].x, b[j].y);
+        bs[j] = pk2(b[j].y, -b[j].x);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const f32x2 ar = pk2(a[i].x, a[i].x), ai = pk2(a[i].y, a[i].y);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          acc[2 * (4 * i + j)] += a[i].x * b[j].x + a[i].y * b[j].y;
-          acc[2 * (4 * i + j) + 1] += a[i].x * b[j].y - a[i].y * b[j].x;
+          fma2(acc2[4 * i + j], ar, bv[j]);
+          fma2(acc2[4 * i + j], ai, bs[j]);
         }
+      }
+    }
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float2 v2 = upk2(acc2[i]);
+      acc[2 * i] = v2.x;
+      acc[2 * i + 1] = v2.y;
     }
     const float v = warp_reduce_scatter32(acc, lane);
     const int e = lane >> 1, i = e >> 2, j = e & 3, c = lane & 1;
@@ -1308,6 +1336,10 @@ __device__ void block_visit_gram(const SvdDesc& P, int bi, int bj, bool first_ro
       }
     }
     __syncthreads();
+  }
+  for (int i = tid; i < GV * GV; i += THREADS) {
+    const float2 q = (&S.Q[0][0])[i];
+    (&S.QS[0][0])[i] = make_float2(-q.y, q.x);
   }
   if (warp == 0) {
     int nr = lrot, nc = lchk;
