@@ -180,11 +180,12 @@ __global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ Z
   __shared__ float4 Bs[ZG_BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  float sr[TT][TT], cr[TT][TT], si[TT][TT], ci[TT][TT];
+  // accumulators as packed pairs: S = (sr, si), C = (cr, ci)
+  f32x2 S2[TT][TT], C2[TT][TT];
 #pragma unroll
   for (int i = 0; i < TT; ++i)
 #pragma unroll
-    for (int j = 0; j < TT; ++j) sr[i][j] = cr[i][j] = si[i][j] = ci[i][j] = 0.f;
+    for (int j = 0; j < TT; ++j) S2[i][j] = C2[i][j] = 0ull;
   const bool a_k_fast = (P.a_cs == 1);
   const bool b_n_fast = (P.b_cs == 1);
   for (int k0 = 0; k0 < P.K; k0 += ZG_BK) {
@@ -236,21 +237,30 @@ __global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ Z
     __syncthreads();
 #pragma unroll 2
     for (int kk = 0; kk < ZG_BK; ++kk) {
-      float4 a[TT], b[TT];
+      // re += a.re b.re - a.im b.im ; im += a.re b.im + a.im b.re, as two packed
+      // compensated accumulations per product (the scalar form's four, in the
+      // same order per lane): (sr, si) += (a.re, a.re) (b.re, b.im), then
+      // (sr, si) += (-a.im, a.im) (b.im, b.re)
+      f32x2 bh[TT], bl[TT], bsh[TT], bsl[TT];
 #pragma unroll
-      for (int i = 0; i < TT; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int j = 0; j < TT; ++j) {
+        const float4 b = Bs[kk][tx + 16 * j];
+        bh[j] = pk2(b.x, b.y);
+        bl[j] = pk2(b.z, b.w);
+        bsh[j] = pk2(b.y, b.x);
+        bsl[j] = pk2(b.w, b.z);
+      }
 #pragma unroll
-      for (int j = 0; j < TT; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < TT; ++i)
+      for (int i = 0; i < TT; ++i) {
+        const float4 a = As[kk][ty + 16 * i];
+        const f32x2 rh = pk2(a.x, a.x), nrh = pk2(-a.x, -a.x), rl = pk2(a.z, a.z);
+        const f32x2 ih = pk2(-a.y, a.y), nih = pk2(a.y, -a.y), il = pk2(-a.w, a.w);
 #pragma unroll
         for (int j = 0; j < TT; ++j) {
-          // re += a.re b.re - a.im b.im ; im += a.re b.im + a.im b.re
-          dd_acc(sr[i][j], cr[i][j], a[i].x, a[i].z, b[j].x, b[j].z);
-          dd_acc(sr[i][j], cr[i][j], -a[i].y, -a[i].w, b[j].y, b[j].w);
-          dd_acc(si[i][j], ci[i][j], a[i].x, a[i].z, b[j].y, b[j].w);
-          dd_acc(si[i][j], ci[i][j], a[i].y, a[i].w, b[j].x, b[j].z);
+          dd_acc2(S2[i][j], C2[i][j], rh, nrh, rl, bh[j], bl[j]);
+          dd_acc2(S2[i][j], C2[i][j], ih, nih, il, bsh[j], bsl[j]);
         }
+      }
     }
     __syncthreads();
   }
@@ -263,7 +273,8 @@ __global__ void __launch_bounds__(256) zgemm_dd_kernel(const __grid_constant__ Z
       int gj = n0 + tx + 16 * j;
       if (gj >= P.N) continue;
       double2* c = P.C + (int64_t)gi * P.c_rs + (int64_t)gj * P.c_cs;
-      double2 v = make_double2((double)sr[i][j] + (double)cr[i][j], (double)si[i][j] + (double)ci[i][j]);
+      const float2 sv = upk2(S2[i][j]), cv = upk2(C2[i][j]);
+      double2 v = make_double2((double)sv.x + (double)cv.x, (double)sv.y + (double)cv.y);
       if (P.accumulate) v = zadd(v, *c);
       *c = v;
     }
