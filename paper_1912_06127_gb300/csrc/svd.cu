@@ -686,15 +686,24 @@ __device__ inline void block_cross(const T* x, const T* y, int lane, typename Pr
   using R = typename Prec<T>::R;
   if constexpr (Prec<T>::dd) {
     // compensated sums (the leading products exact, the rest in FP32): the
-    // result carries ~48 bits, as if summed in double-float
-    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    // result carries ~48 bits, as if summed in double-float. Packed (re, im)
+    // lanes: (sr, si) += (re u, re u) (re v, im v), then (sr, si) +=
+    // (im u, -im u) (im v, re v) -- per lane the operations and the order of
+    // four scalar accumulations
+    f32x2 acc_s = 0ull, acc_c = 0ull;
 #pragma unroll 4
     for (int i = 0; i < C::EPT; ++i) {
       const float4 u = x[lane + 32 * i], v = y[lane + 32 * i];
-      dd_acc(sr, cr, u.x, u.z, v.x, v.z);    // re(u) re(v)
-      dd_acc(sr, cr, u.y, u.w, v.y, v.w);    // im(u) im(v)
-      dd_acc(si, ci, u.x, u.z, v.y, v.w);    // re(u) im(v)
-      dd_acc(si, ci, -u.y, -u.w, v.x, v.z);  // -im(u) re(v)
+      dd_acc2(acc_s, acc_c, pk2(u.x, u.x), pk2(-u.x, -u.x), pk2(u.z, u.z), pk2(v.x, v.y), pk2(v.z, v.w));
+      dd_acc2(acc_s, acc_c, pk2(u.y, -u.y), pk2(-u.y, u.y), pk2(u.w, -u.w), pk2(v.y, v.x), pk2(v.w, v.z));
+    }
+    float sr, si, cr, ci;
+    {
+      const float2 sv = upk2(acc_s), cv = upk2(acc_c);
+      sr = sv.x;
+      si = sv.y;
+      cr = cv.x;
+      ci = cv.y;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -719,6 +728,21 @@ __device__ inline void block_cross(const T* x, const T* y, int lane, typename Pr
     kr = Prec<T>::wsum(a);
     ki = Prec<T>::wsum(b);
   }
+}
+
+// dd_axpy3 on packed (re, im) lanes: s, c = hi, lo of x; term k is
+// (ph_k, pl_k) (qh_k, ql_k) with nph_k = -ph_k
+__device__ inline void dd_axpy3_2(f32x2 s, f32x2 c, f32x2 p1h, f32x2 n1h, f32x2 p1l, f32x2 q1h, f32x2 q1l,
+                                  f32x2 p2h, f32x2 n2h, f32x2 p2l, f32x2 q2h, f32x2 q2l, f32x2 p3h, f32x2 n3h,
+                                  f32x2 p3l, f32x2 q3h, f32x2 q3l, float4& o) {
+  dd_acc2(s, c, p1h, n1h, p1l, q1h, q1l);
+  dd_acc2(s, c, p2h, n2h, p2l, q2h, q2l);
+  dd_acc2(s, c, p3h, n3h, p3l, q3h, q3l);
+  // fast_two_sum(s, c) per lane
+  const f32x2 oh = add2(s, c);
+  const f32x2 ol = sub2(c, sub2(oh, s));
+  const float2 h = upk2(oh), l = upk2(ol);
+  o = make_float4(h.x, h.y, l.x, l.y);
 }
 
 // o = x + sum_k p_k q_k in double-float (x, p_k, q_k given as hi/lo pairs)
@@ -826,16 +850,23 @@ __device__ inline void block_local_round(typename Prec<T>::R tol2, typename Prec
       const float2 c1 = make_float2(rec.cm1, rec.cm1l);
       const float2 a1 = make_float2(rec.m1f.x, rec.m1l.x), b1 = make_float2(rec.m1f.y, rec.m1l.y);
       const float2 a2 = make_float2(rec.m2f.x, rec.m2l.x), b2 = make_float2(rec.m2f.y, rec.m2l.y);
+      // the (re, im) lanes packed: term 1 (cs - 1) x, term 2 m re-part times y,
+      // term 3 (-im m, im m) times (im y, re y)
+      const f32x2 c1h = pk2(c1.x, c1.x), c1n = pk2(-c1.x, -c1.x), c1l = pk2(c1.y, c1.y);
+      const f32x2 a1h = pk2(a1.x, a1.x), a1n = pk2(-a1.x, -a1.x), a1l = pk2(a1.y, a1.y);
+      const f32x2 b1h = pk2(-b1.x, b1.x), b1n = pk2(b1.x, -b1.x), b1l = pk2(-b1.y, b1.y);
+      const f32x2 a2h = pk2(a2.x, a2.x), a2n = pk2(-a2.x, -a2.x), a2l = pk2(a2.y, a2.y);
+      const f32x2 b2h = pk2(-b2.x, b2.x), b2n = pk2(b2.x, -b2.x), b2l = pk2(-b2.y, b2.y);
 #pragma unroll 2
       for (int i = 0; i < C::EPT; ++i) {
         const float4 u = x[lane + 32 * i], v = y[lane + 32 * i];
+        const f32x2 uh = pk2(u.x, u.y), ul = pk2(u.z, u.w), vh = pk2(v.x, v.y), vl = pk2(v.z, v.w);
+        const f32x2 uhs = pk2(u.y, u.x), uls = pk2(u.w, u.z), vhs = pk2(v.y, v.x), vls = pk2(v.w, v.z);
         float4 nu, nv;
         // re x' = re u + c1 re u + a1 re v - b1 im v ; im x' = im u + c1 im u + a1 im v + b1 re v
-        dd_axpy3(u.x, u.z, c1.x, c1.y, u.x, u.z, a1.x, a1.y, v.x, v.z, -b1.x, -b1.y, v.y, v.w, nu.x, nu.z);
-        dd_axpy3(u.y, u.w, c1.x, c1.y, u.y, u.w, a1.x, a1.y, v.y, v.w, b1.x, b1.y, v.x, v.z, nu.y, nu.w);
+        dd_axpy3_2(uh, ul, c1h, c1n, c1l, uh, ul, a1h, a1n, a1l, vh, vl, b1h, b1n, b1l, vhs, vls, nu);
         // re y' = re v + c1 re v + a2 re u - b2 im u ; im y' = im v + c1 im v + a2 im u + b2 re u
-        dd_axpy3(v.x, v.z, c1.x, c1.y, v.x, v.z, a2.x, a2.y, u.x, u.z, -b2.x, -b2.y, u.y, u.w, nv.x, nv.z);
-        dd_axpy3(v.y, v.w, c1.x, c1.y, v.y, v.w, a2.x, a2.y, u.y, u.w, b2.x, b2.y, u.x, u.z, nv.y, nv.w);
+        dd_axpy3_2(vh, vl, c1h, c1n, c1l, vh, vl, a2h, a2n, a2l, uh, ul, b2h, b2n, b2l, uhs, uls, nv);
         x[lane + 32 * i] = nu;
         y[lane + 32 * i] = nv;
       }
