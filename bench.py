@@ -509,8 +509,8 @@ def fp64_peak_tflops():
 # launch of the time step carries several problems and its traffic scales with
 # them. Emptied whenever a listed kernel changes after its capture, so that no
 # stale figure is reported.
-TRAFFIC_PER_PROBLEM = {"svd_jacobi_fp32": 0.5 * (4.654592e6 + 5.826304e6 + 5.539584e6 + 7.131136e6),
-                       "svd_jacobi_dd": 0.5 * (8.790528e6 + 0.018688e6 + 8.682496e6 + 0.021760e6)}
+TRAFFIC_PER_PROBLEM = {"svd_jacobi_fp32": 4.756224e6 + 0.859392e6,
+                       "svd_jacobi_dd": 8.530432e6 + 0.985856e6}
 
 
 def sm_count():
