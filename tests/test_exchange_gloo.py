@@ -5,10 +5,11 @@ With one GPU per group of segments, the ranks would run the stages in
 lockstep and exchange, at every boundary update between two ranks, the
 tensors of tdvp_exchange_plan (the right rank's Psi_{e+1} and gamma_{e+1}
 before it, the left rank's Psi_{e+1}, V_e and beta_{e+1} after it). This test
-checks that plan: two CPU ranks each run the oracle's local operations for
-their own segments only, send and receive exactly the planned tensors, and
-must end with the one-rank oracle's state bit for bit -- for the two-site
-sweep and the segmented one-site sweep.
+checks that plan: two or three CPU ranks (the middle one exchanging with both
+neighbours) each run the oracle's local operations for their own segments
+only, send and receive exactly the planned tensors, and must end with the
+one-rank oracle's state bit for bit -- for the two-site sweep and the
+segmented one-site sweep.
 """
 import os
 import socket
@@ -22,6 +23,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 N = 14
 SEG = [3, 4, 4, 3]
 RANK_OF_SEG = [0, 0, 1, 1]
+# the segment layouts run: two ranks with one boundary between them, and three
+# ranks where the middle one exchanges with both neighbours
+LAYOUTS = {"two_ranks": ([3, 4, 4, 3], [0, 0, 1, 1]), "three_ranks": ([3, 3, 3, 3, 2], [0, 1, 1, 2, 2])}
 
 
 def _free_port():
@@ -30,7 +34,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _setup():
+def _setup(seg):
     import tdvp_inputs as I
     from oracle import models
     from oracle import mps as M
@@ -38,7 +42,7 @@ def _setup():
     x, lam = models.fit_power_law(2.0, 3, N - 1)
     W = models.build_mpo_site(models.ISING, 1.0, 0.7, x, lam)
     mps = M.canonicalize(I.random_mps_tensors(N, 6, seed=21), 8, 1e-14)
-    p = T.Params(dt=0.04, chi_max=8, krylov_max=12, krylov_tol=0.0, seg_len=SEG)
+    p = T.Params(dt=0.04, chi_max=8, krylov_max=12, krylov_tol=0.0, seg_len=seg)
     return W, mps, p
 
 
@@ -63,7 +67,7 @@ def _recv(dist, torch, src):
     return (a.view(np.complex128) if is_c else a).reshape(shape).copy()
 
 
-def _rank_main(rank, world, port, scheme, steps, out):
+def _rank_main(rank, world, port, scheme, steps, seg, rank_of_seg, out):
     os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
     sys.path.insert(0, ROOT)
     import torch
@@ -72,14 +76,14 @@ def _rank_main(rank, world, port, scheme, steps, out):
     from oracle import tdvp1 as T1
     from paper_1912_06127_gb300 import tdvp
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    W, mps, p = _setup()
+    W, mps, p = _setup(seg)
     eng = T.Engine(mps, W)
-    bounds = T.segment_bounds(N, SEG)
-    mine = {k for k in range(len(SEG)) if RANK_OF_SEG[k] == rank}
-    owner = {j: RANK_OF_SEG[k] for k, (s, e) in enumerate(bounds) for j in range(s, e + 1)}
-    halves = ([T.build_half(N, SEG, h, p.merge_turning) for h in (1, 2)] if scheme == 2 else
-              [T1.build_half1(N, SEG, h, p.merge_turning) for h in (1, 2)])
-    plans = [tdvp.exchange_plan(N, SEG, RANK_OF_SEG, scheme, p.merge_turning, h) for h in (1, 2)]
+    bounds = T.segment_bounds(N, seg)
+    mine = {k for k in range(len(seg)) if rank_of_seg[k] == rank}
+    owner = {j: rank_of_seg[k] for k, (s, e) in enumerate(bounds) for j in range(s, e + 1)}
+    halves = ([T.build_half(N, seg, h, p.merge_turning) for h in (1, 2)] if scheme == 2 else
+              [T1.build_half1(N, seg, h, p.merge_turning) for h in (1, 2)])
+    plans = [tdvp.exchange_plan(N, seg, rank_of_seg, scheme, p.merge_turning, h) for h in (1, 2)]
     store = {0: eng.mps.Psi, 1: eng.mps.V, 2: eng.beta, 3: eng.gamma}
     n_sent = 0
 
@@ -96,9 +100,9 @@ def _rank_main(rank, world, port, scheme, steps, out):
 
     for _ in range(steps):
         if scheme == 1:   # step1_segmented's rebuilds at the start of a step, by the owning ranks
-            if owner[0] == rank and T.sweeps_right_first(0, len(SEG)):
+            if owner[0] == rank and T.sweeps_right_first(0, len(seg)):
                 eng.gamma[0] = T.env_right(eng.gamma[1], eng._B(0), W)
-            if owner[N - 1] == rank and not T.sweeps_right_first(len(SEG) - 1, len(SEG)):
+            if owner[N - 1] == rank and not T.sweeps_right_first(len(seg) - 1, len(seg)):
                 eng.beta[N - 1] = T.env_left(eng.beta[N - 2], eng._A(N - 2), W)
         for ops, plan in zip(halves, plans):
             for stage in range(max(o.stage for o in ops) + 1):
@@ -133,8 +137,9 @@ def _rank_main(rank, world, port, scheme, steps, out):
     dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("layout", sorted(LAYOUTS))
 @pytest.mark.parametrize("scheme", [2, 1], ids=["two_site", "one_site"])
-def test_two_ranks_reproduce_one_rank(scheme):
+def test_ranks_reproduce_one_rank(scheme, layout):
     pytest.importorskip("torch")
     import torch.multiprocessing as mp
     sys.path.insert(0, ROOT)
@@ -143,21 +148,24 @@ def test_two_ranks_reproduce_one_rank(scheme):
     from oracle import tdvp as T
     from oracle import tdvp1 as T1
     steps = 2
+    seg, rank_of_seg = LAYOUTS[layout]
+    world = max(rank_of_seg) + 1
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, scheme, steps, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, scheme, steps, seg, rank_of_seg, q))
+             for r in range(world)]
     for pr in procs:
         pr.start()
     res = {}
-    for _ in range(2):
+    for _ in range(world):
         r, psi, v, n_sent = q.get(timeout=300)
         res[r] = (psi, v, n_sent)
     for pr in procs:
         pr.join(timeout=60)
         assert pr.exitcode == 0
     # one rank, the oracle's own sweep
-    W, mps, p = _setup()
+    W, mps, p = _setup(seg)
     eng = T.Engine(mps, W)
     if scheme == 2:
         eng.step(p, steps)
@@ -168,9 +176,14 @@ def test_two_ranks_reproduce_one_rank(scheme):
         assert np.array_equal(psi[j], eng.mps.Psi[j]), j
     for j in range(N - 1):
         assert np.array_equal(v[j], eng.mps.V[j]), j
-    # one boundary between the ranks (after segment 1), updated once per half:
-    # 2 messages before and 3 after, per half and step
-    assert res[0][2] + res[1][2] == steps * 2 * 5
+    # exactly the planned messages were sent: 2 before and 3 after each update
+    # of a boundary between two ranks
+    from paper_1912_06127_gb300 import tdvp
+    planned = sum(len(tdvp.exchange_plan(N, seg, rank_of_seg, scheme, p.merge_turning, h)) for h in (1, 2))
+    assert planned % 5 == 0 and sum(r[2] for r in res.values()) == steps * planned
+    if layout == "two_ranks":
+        # the one boundary between the ranks (after segment 1) is updated in both halves
+        assert planned == 2 * 5
 
 
 def test_exchange_plan_host_rules():
